@@ -1,0 +1,92 @@
+"""Pins for the oracle's ILUT(d, p) and its triangular sweeps (Sec. II)."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from oracle.reorder_factor import ilut
+
+
+def diag_dominant(rng, n, density):
+    """Sparse complex matrix whose columns are strictly diagonally dominant, so
+    that Gaussian elimination with partial pivoting picks the diagonal."""
+    M = sp.random(n, n, density=density, random_state=rng, format="csr")
+    M = M + 1j * sp.random(n, n, density=density, random_state=rng, format="csr")
+    M = M.toarray()
+    np.fill_diagonal(M, 0)
+    colsum = np.abs(M).sum(axis=0)
+    M = M + np.diag(colsum + 1.0 + rng.uniform(0, 1, n))
+    return sp.csr_matrix(M)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_no_dropping_gives_complete_lu(seed):
+    """d = 0 and an unbounded fill cap give the complete LU factorisation
+    (Sec. II: with d = 0 the iLU returns the complete factorisation)."""
+    rng = np.random.default_rng(seed)
+    n = 40
+    A = diag_dominant(rng, n, 0.08)
+    F = ilut(A, 0.0, 1e6)
+    P, Lr, Ur = sla.lu(A.toarray())
+    np.testing.assert_allclose(P, np.eye(n))  # no pivoting happened in LAPACK either
+    np.testing.assert_allclose(F.L().toarray(), Lr, atol=1e-13)
+    np.testing.assert_allclose(F.U().toarray(), Ur, atol=1e-13)
+    assert F.n_guarded == 0
+
+
+def test_hand_worked_dropping():
+    """A 3x3 case worked by hand.
+
+    A = [[4, 0, 1], [2, 4, 0.01], [0, 1, 4]], d = 0.1, p large.
+    Row 1: ||row||_inf = 4, tau = 0.4.  l10 = 2/4 = 0.5 >= tau -> kept;
+    w = row1 - 0.5*row0 = [., 4, 0.01 - 0.5] = [., 4, -0.49];  |-0.49| >= 0.4 kept.
+    Row 2: tau = 0.4; l21 = 1/4 = 0.25 < tau -> dropped (no elimination);
+    u22 = 4.
+    """
+    A = sp.csr_matrix(np.array([[4, 0, 1], [2, 4, 0.01], [0, 1, 4]], dtype=complex))
+    F = ilut(A, 0.1, 100.0)
+    np.testing.assert_allclose(F.L().toarray(), [[1, 0, 0], [0.5, 1, 0], [0, 0, 1]])
+    np.testing.assert_allclose(F.U().toarray(), [[4, 0, 1], [0, 4, -0.49], [0, 0, 4]])
+
+
+def test_small_original_entries_are_dropped():
+    """Sec. IV: entries below the tolerance are absent from the factors even
+    when they are entries of A (the 1e-15 thermal terms)."""
+    A = sp.csr_matrix(np.array([[2, 1e-15, 0], [1e-15, 2, 1], [0, 1, 2]], dtype=complex))
+    F = ilut(A, 1e-4, 100.0)
+    assert 1 not in F.ui[F.up[0]:F.up[1]]
+    assert F.nnz_l == 1  # only l21
+
+
+def test_fill_cap_per_row():
+    rng = np.random.default_rng(7)
+    A = diag_dominant(rng, 60, 0.15)
+    p = 1.0
+    F = ilut(A, 0.0, p)
+    nnz = np.diff(A.indptr)
+    cap = np.maximum(np.floor(p * nnz / 2), 1)
+    assert np.all(np.diff(F.lp) <= cap)
+    assert np.all(np.diff(F.up) <= cap)
+    assert F.nnz_l + F.nnz_u <= p * A.nnz
+    # kept entries of each L row are the largest of the unrestricted row
+    assert F.fill_factor(A.nnz) <= p
+
+
+def test_pivot_guard():
+    A = sp.csr_matrix(np.array([[1, 1], [1, 1]], dtype=complex))
+    F = ilut(A, 0.0, 100.0)
+    assert F.n_guarded == 1
+    assert abs(F.ux[F.up[1]]) == pytest.approx(1e-14)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_sweeps_against_dense_solves(seed):
+    rng = np.random.default_rng(seed + 10)
+    n = 50
+    A = diag_dominant(rng, n, 0.1)
+    F = ilut(A, 1e-2, 3.0)
+    Ld, Ud = F.L().toarray(), F.U().toarray()
+    M = Ld @ Ud
+    v = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    np.testing.assert_allclose(F.solve(v), np.linalg.solve(M, v), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(F.solve_h(v), np.linalg.solve(M.conj().T, v), rtol=1e-12, atol=1e-12)
