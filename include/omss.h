@@ -1,0 +1,185 @@
+/*
+ * omss -- steady states of driven, damped optomechanical systems on GB300.
+ *
+ * C ABI of the CUDA library (libomss.so) that implements the iterative
+ * steady-state solve of Nation, Johansson, Blencowe & Rimberg, "Iterative
+ * solutions to the steady state density matrix for optomechanical systems"
+ * (arXiv:1411.4356):
+ *
+ *   om_build_liouvillian  Eq. 1 (Hamiltonian), Eq. 3 (Lindblad form), Eq. 4
+ *                         (column stacking), Eq. 5 (trace augmentation)
+ *   om_permute            Sec. III: reverse Cuthill-McKee order of the
+ *                         structure of L~ + L~^T, applied to rows and columns
+ *   om_ilu_factor         Sec. II: incomplete LU with dual threshold (d, p)
+ *   om_steady_state_solve Sec. IV: restarted GMRES with the ILU preconditioner
+ *                         (Eq. 6), trace normalisation, rho in natural order
+ *   om_steady_state_adjoint  gradients of Tr(O rho) by the adjoint equation
+ *                         L~^H mu = dF/drho with the same permuted ILU
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Complex numbers are complex128 stored as interleaved (re, im) doubles
+ *   ("c128"); complex64 as interleaved floats ("c64").
+ * - Device pointers are CUDA device addresses on the current device; host
+ *   pointers are ordinary host memory.  Each argument states which.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  All device work is ordered on it.  Entry points that return
+ *   host-side scalars synchronise the stream before returning.
+ * - Handles (om_matrix, om_ilu) own device memory allocated by the library
+ *   (cudaMallocAsync on the given stream) and are released with the matching
+ *   *_free call.  Vectors (rho, perm, x0, gradients of rho) are caller-owned.
+ * - No C++ exception crosses the ABI.  Every call returns an om_status;
+ *   OM_OK is 0 and every error is negative.  om_last_error() returns a
+ *   human-readable message for the calling thread's most recent error.
+ * - Vectorisation (Eq. 4): rho_ij sits at k = i + j n (column stacking);
+ *   Hilbert index of |c, m> is h = c N_m + m (a = a (x) I_b, Sec. III).
+ */
+#ifndef OMSS_H
+#define OMSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    OM_OK = 0,
+    OM_EINVAL = -1,      /* bad argument (null pointer, size out of range, ...) */
+    OM_ENOMEM = -2,      /* device or host allocation failed */
+    OM_ECUDA = -3,       /* a CUDA runtime call failed */
+    OM_EZEROPIVOT = -4,  /* ILU produced a zero pivot that the guard could not fix */
+    OM_ENOCONV = -5,     /* GMRES hit max_iters; the best iterate is still written */
+    OM_EBREAKDOWN = -6,  /* Arnoldi breakdown before convergence */
+    OM_ENUMERIC = -7,    /* NaN or Inf met in a residual or a factor */
+    OM_ETIMEOUT = -8     /* a device-side wait exceeded wait_timeout_ns */
+} om_status;
+
+/* Parameters of Eq. 1 and Eq. 3 (units of omega_m) and the Fock cutoffs of
+ * Sec. III.  Gamma_m = omega_m / Q_m. */
+typedef struct {
+    int32_t Nc, Nm;
+    double omega_m, Delta, kappa, g0, E, Q_m, n_th;
+} om_params;
+
+typedef struct {
+    int32_t trace_mode; /* 0: row 0 of L~ is w T alone ("replace");
+                           1: L~ = L + w T as printed in Eq. 5 ("add") */
+    double nth_floor;   /* if n_th == 0, use this occupation instead (Sec. IV
+                           uses 1e-15); 0 keeps n_th = 0 */
+} om_build_opts;
+
+typedef struct {
+    int32_t restart;        /* GMRES restart length m (Sec. IV restarts at 10) */
+    int32_t max_iters;      /* cap on inner iterations over all cycles */
+    int32_t precision;      /* 0: complex128 throughout;
+                               1: complex64 inner GMRES / ILU / SpMV inside an
+                                  FP64 iterative-refinement loop */
+    int32_t reserved;
+    double tol;             /* target of eta = ||L x||_inf / (||L||_inf ||x||_inf) */
+    int64_t wait_timeout_ns;/* bound on any device spin-wait (0: 2 s default) */
+} om_solve_opts;
+
+typedef struct {
+    int32_t iterations;     /* inner GMRES iterations, all cycles */
+    int32_t cycles;         /* restarts + 1 (FP64 path) or refinement steps (mixed) */
+    double eta;             /* final normwise backward error (see om_solve_opts.tol) */
+    double trace_before;    /* Tr(x) before normalisation */
+    double seconds;         /* wall time of the call */
+    double residual_history[64]; /* eta at the end of each cycle (first 64) */
+} om_solve_info;
+
+typedef struct om_matrix om_matrix; /* complex CSR on the device */
+typedef struct om_ilu om_ilu;       /* ILU factors + sweep schedule on the device */
+
+/* ---- Eq. 1-5: assemble L~ ------------------------------------------------
+ * Builds the trace-augmented Liouvillian L~ (N = (Nc*Nm)^2 rows) in CSR with
+ * int64 row pointers, int32 columns sorted within each row and c128 values,
+ * exact zeros dropped.  w = mean of diag(L) (Sec. IV) is kept in the handle,
+ * as are ||L||_inf and the unmodified row 0 of L (for the residual eta).
+ * Errors: OM_EINVAL if a pointer is NULL, Nc or Nm < 1, N > 2^31 - 1 or the
+ * nonzero count exceeds 2^31 - 1. */
+om_status om_build_liouvillian(const om_params *params, const om_build_opts *opts,
+                               void *stream, om_matrix **out);
+
+/* Host-side description of a matrix handle; any out pointer may be NULL. */
+om_status om_matrix_info(const om_matrix *A, int64_t *nrows, int64_t *nnz, double *w,
+                         double *norm_inf);
+
+/* Copies the CSR arrays to caller-owned HOST buffers of sizes nrows+1, nnz,
+ * 2*nnz doubles (any may be NULL to skip).  Synchronises `stream`. */
+om_status om_matrix_export(const om_matrix *A, int64_t *rowptr, int32_t *col, double *val,
+                           void *stream);
+
+/* ---- Sec. III: reverse Cuthill-McKee ----------------------------------------
+ * perm_dev (caller-owned DEVICE int32[N]) receives perm[new] = old, the RCM
+ * order of the structure of A + A^T (degree = nonzeros of a row of that
+ * structure; each component starts at the unvisited node of least (degree,
+ * index); neighbours are queued in increasing (degree, index); the
+ * Cuthill-McKee order is reversed).  *A_rcm = P A P^T with
+ * A_rcm[r, c] = A[perm[r], perm[c]].  Errors: OM_EINVAL on NULL arguments. */
+om_status om_permute(const om_matrix *A, void *stream, int32_t *perm_dev, om_matrix **A_rcm);
+
+/* ---- Sec. II: ILUT(d, p) ----------------------------------------------------
+ * Row-wise incomplete LU of A (unit L, no pivoting).  In row i every entry
+ * of modulus below droptol * ||row i of A||_inf is dropped (the diagonal is
+ * kept); the strict-L part keeps at most floor(fill * nnz_i / 2) entries and
+ * the U part, diagonal included, at most as many (largest moduli, ties to
+ * the smaller column), so NNZ(L) + NNZ(U) <= fill * NNZ(A).  A pivot below
+ * 1e-14 ||row i||_inf is replaced by that value and counted.
+ * flags bit 0: add the moduli of the entries dropped from row i to |u_ii|
+ * (diagonal compensation).  Errors: OM_EINVAL, OM_ENOMEM. */
+om_status om_ilu_factor(const om_matrix *A_rcm, double droptol, double fill, int32_t flags,
+                        void *stream, om_ilu **out);
+
+/* Statistics of a factorisation (any out pointer may be NULL). */
+om_status om_ilu_info(const om_ilu *M, int64_t *nnz_l, int64_t *nnz_u, int64_t *n_guarded,
+                      int64_t *levels_l, int64_t *levels_u);
+
+/* ---- Sec. IV: the steady state ----------------------------------------------
+ * Solves L~_rcm x = P (w, 0, ...)^T by restarted GMRES(m) with right
+ * preconditioning M = L U (the system of Eq. 6), stops when eta <= tol,
+ * divides x by its trace and scatters it back to natural order:
+ * rho_dev (caller-owned DEVICE c128[n*n], column-major n x n) receives rho.
+ * perm_dev is the DEVICE permutation written by om_permute.  x0 (DEVICE c128
+ * [N] in permuted order) may be NULL.  info (HOST) may be NULL.
+ * Errors: OM_EINVAL, OM_ENOMEM, OM_ENOCONV (rho still written),
+ * OM_ENUMERIC, OM_ETIMEOUT, OM_ECUDA. */
+om_status om_steady_state_solve(const om_matrix *A_rcm, const om_ilu *M, const int32_t *perm_dev,
+                                const om_solve_opts *opts, const double *x0, double *rho_dev,
+                                om_solve_info *info, void *stream);
+
+/* ---- adjoint ------------------------------------------------------------------
+ * For a real loss F(rho) with gradient G = dF/dRe(rho) + i dF/dIm(rho)
+ * (DEVICE c128[n*n], column-major), solves L~^H mu = G (GMRES with the
+ * preconditioner (L U)^H, i.e. sweeps with U^H then L^H) and writes
+ * grad_out (HOST double[4]) = dF/d(Delta, E, g0, kappa) = -Re(mu^H dL~/dtheta rho),
+ * dL~/dtheta being dL/dtheta in the rows of L and zero in a replaced trace
+ * row.  params must be those A_rcm was built from.  rho_dev is the solution
+ * written by om_steady_state_solve.  Errors as om_steady_state_solve. */
+om_status om_steady_state_adjoint(const om_matrix *A_rcm, const om_ilu *M, const int32_t *perm_dev,
+                                  const om_solve_opts *opts, const om_params *params,
+                                  const double *rho_dev, const double *grad_rho_dev,
+                                  double grad_out[4], om_solve_info *info, void *stream);
+
+/* ---- single kernels, exposed for parity tests -------------------------------
+ * y = A x (DEVICE c128 vectors of length nrows). */
+om_status om_spmv(const om_matrix *A, const double *x, double *y, void *stream);
+/* z = (L U)^{-1} v, or (L U)^{-H} v when conj_transpose != 0 (DEVICE c128[N]).
+ * z and v may alias. */
+om_status om_ilu_apply(const om_ilu *M, int32_t conj_transpose, const double *v, double *z,
+                       void *stream);
+/* <a^dag a>, <b^dag b> of a DEVICE rho (c128 n x n column-major); out HOST double[2]. */
+om_status om_observables(int32_t Nc, int32_t Nm, const double *rho_dev, double out[2],
+                         void *stream);
+
+void om_matrix_free(om_matrix *A);
+void om_ilu_free(om_ilu *M);
+const char *om_status_str(om_status s);
+const char *om_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OMSS_H */

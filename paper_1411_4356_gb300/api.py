@@ -1,0 +1,213 @@
+"""Python binding of the omss C ABI (argument marshalling only).
+
+Every step of the solve runs in libomss.so; PyTorch supplies CUDA device
+memory and the current stream.  Names follow include/omss.h without the
+``om_`` prefix.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check, om_build_opts, om_params, om_solve_info, om_solve_opts
+from .workloads import SystemParams
+
+TRACE_MODES = {"replace": 0, "add": 1}
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _require_cuda(t: torch.Tensor, dtype, numel: int, name: str):
+    if not t.is_cuda or t.dtype != dtype or t.numel() != numel or not t.is_contiguous():
+        raise ValueError(f"{name}: need a contiguous CUDA {dtype} tensor with {numel} elements")
+
+
+def to_om_params(p: SystemParams) -> om_params:
+    return om_params(p.Nc, p.Nm, p.omega_m, p.Delta, p.kappa, p.g0, p.E, p.Q_m, p.n_th)
+
+
+class Matrix:
+    """Device CSR handle (om_matrix)."""
+
+    def __init__(self, handle: int, params: SystemParams):
+        self._h = ctypes.c_void_p(handle)
+        self.params = params
+        lib = _lib.load()
+        N, nnz, w, ninf = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        check(lib.om_matrix_info(self._h, ctypes.byref(N), ctypes.byref(nnz), ctypes.byref(w), ctypes.byref(ninf)),
+              "om_matrix_info")
+        self.N, self.nnz, self.w, self.norm_inf = N.value, nnz.value, w.value, ninf.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def export(self, stream=None):
+        """(rowptr int64, col int32, val complex128) numpy copies."""
+        rp = np.empty(self.N + 1, dtype=np.int64)
+        ci = np.empty(self.nnz, dtype=np.int32)
+        va = np.empty(self.nnz, dtype=np.complex128)
+        check(_lib.load().om_matrix_export(self._h, rp.ctypes.data_as(ctypes.c_void_p),
+                                           ci.ctypes.data_as(ctypes.c_void_p), va.ctypes.data_as(ctypes.c_void_p),
+                                           ctypes.c_void_p(_stream(stream))), "om_matrix_export")
+        return rp, ci, va
+
+    def free(self):
+        if self._h:
+            _lib.load().om_matrix_free(self._h)
+            self._h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class ILU:
+    """ILU factors handle (om_ilu)."""
+
+    def __init__(self, handle: int, nnz_a: int):
+        self._h = ctypes.c_void_p(handle)
+        vals = [ctypes.c_int64() for _ in range(5)]
+        check(_lib.load().om_ilu_info(self._h, *[ctypes.byref(v) for v in vals]), "om_ilu_info")
+        self.nnz_l, self.nnz_u, self.n_guarded, self.levels_l, self.levels_u = (v.value for v in vals)
+        self.fill = (self.nnz_l + self.nnz_u) / nnz_a
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if self._h:
+            _lib.load().om_ilu_free(self._h)
+            self._h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def build_liouvillian(params: SystemParams, trace_mode: str = "replace", nth_floor: float = 1e-15,
+                      stream=None) -> Matrix:
+    """Eq. 1-5: trace-augmented Liouvillian on the device."""
+    lib = _lib.load()
+    out = ctypes.c_void_p()
+    p = to_om_params(params)
+    o = om_build_opts(TRACE_MODES[trace_mode], nth_floor)
+    check(lib.om_build_liouvillian(ctypes.byref(p), ctypes.byref(o), ctypes.c_void_p(_stream(stream)),
+                                   ctypes.byref(out)), "om_build_liouvillian")
+    return Matrix(out.value, params)
+
+
+def permute(A: Matrix, stream=None):
+    """Sec. III: (A_rcm, perm) with perm[new] = old as a CUDA int32 tensor."""
+    lib = _lib.load()
+    perm = torch.empty(A.N, dtype=torch.int32, device="cuda")
+    out = ctypes.c_void_p()
+    check(lib.om_permute(A.handle, ctypes.c_void_p(_stream(stream)), _ptr(perm), ctypes.byref(out)), "om_permute")
+    return Matrix(out.value, A.params), perm
+
+
+def ilu_factor(A: Matrix, droptol: float, fill: float, compensate: bool = False, stream=None) -> ILU:
+    """Sec. II: ILUT(droptol, fill) of a permuted matrix."""
+    lib = _lib.load()
+    out = ctypes.c_void_p()
+    check(lib.om_ilu_factor(A.handle, float(droptol), float(fill), 1 if compensate else 0,
+                            ctypes.c_void_p(_stream(stream)), ctypes.byref(out)), "om_ilu_factor")
+    return ILU(out.value, A.nnz)
+
+
+@dataclass
+class SolveInfo:
+    iterations: int
+    cycles: int
+    eta: float
+    trace_before: float
+    seconds: float
+    residual_history: list
+    status: int
+
+
+def _opts(restart, max_iters, tol, precision, wait_timeout_ns):
+    return om_solve_opts(int(restart), int(max_iters), int(precision), 0, float(tol), int(wait_timeout_ns))
+
+
+def steady_state_solve(A_rcm: Matrix, M: ILU, perm: torch.Tensor, restart: int = 30, max_iters: int = 5000,
+                       tol: float = 1e-10, precision: int = 0, x0: torch.Tensor | None = None,
+                       wait_timeout_ns: int = 0, stream=None, raise_on_noconv: bool = True,
+                       rho_out: torch.Tensor | None = None):
+    """Sec. IV: rho (n x n complex128 CUDA tensor, rho[i, j] = rho_ij) and SolveInfo."""
+    lib = _lib.load()
+    n = A_rcm.params.Nc * A_rcm.params.Nm
+    _require_cuda(perm, torch.int32, A_rcm.N, "perm")
+    flat = rho_out if rho_out is not None else torch.empty(n * n, dtype=torch.complex128, device="cuda")
+    _require_cuda(flat, torch.complex128, n * n, "rho_out")
+    if x0 is not None:
+        _require_cuda(x0, torch.complex128, A_rcm.N, "x0")
+    o = _opts(restart, max_iters, tol, precision, wait_timeout_ns)
+    info = om_solve_info()
+    st = lib.om_steady_state_solve(A_rcm.handle, M.handle, _ptr(perm), ctypes.byref(o), _ptr(x0), _ptr(flat),
+                                   ctypes.byref(info), ctypes.c_void_p(_stream(stream)))
+    si = SolveInfo(info.iterations, info.cycles, info.eta, info.trace_before, info.seconds,
+                   list(info.residual_history[:min(info.cycles, 64)]), st)
+    if st != 0 and not (st == -5 and not raise_on_noconv):
+        check(st, "om_steady_state_solve")
+    return flat.view(n, n).t(), si
+
+
+def steady_state_adjoint(A_rcm: Matrix, M: ILU, perm: torch.Tensor, rho: torch.Tensor, grad_rho: torch.Tensor,
+                         restart: int = 30, max_iters: int = 5000, tol: float = 1e-10, wait_timeout_ns: int = 0,
+                         stream=None):
+    """dF/d(Delta, E, g0, kappa) for a real loss with grad_rho = dF/dRe(rho) + i dF/dIm(rho)."""
+    lib = _lib.load()
+    n = A_rcm.params.Nc * A_rcm.params.Nm
+    rho_flat = rho.t().contiguous().view(-1) if rho.dim() == 2 else rho
+    g_flat = grad_rho.t().contiguous().view(-1) if grad_rho.dim() == 2 else grad_rho.contiguous()
+    _require_cuda(rho_flat, torch.complex128, n * n, "rho")
+    _require_cuda(g_flat, torch.complex128, n * n, "grad_rho")
+    o = _opts(restart, max_iters, tol, 0, wait_timeout_ns)
+    p = to_om_params(A_rcm.params)
+    out = (ctypes.c_double * 4)()
+    info = om_solve_info()
+    check(lib.om_steady_state_adjoint(A_rcm.handle, M.handle, _ptr(perm), ctypes.byref(o), ctypes.byref(p),
+                                      _ptr(rho_flat), _ptr(g_flat), ctypes.byref(out), ctypes.byref(info),
+                                      ctypes.c_void_p(_stream(stream))), "om_steady_state_adjoint")
+    return list(out), SolveInfo(info.iterations, info.cycles, info.eta, info.trace_before, info.seconds,
+                                list(info.residual_history[:min(info.cycles, 64)]), 0)
+
+
+def spmv(A: Matrix, x: torch.Tensor, stream=None) -> torch.Tensor:
+    _require_cuda(x, torch.complex128, A.N, "x")
+    y = torch.empty_like(x)
+    check(_lib.load().om_spmv(A.handle, _ptr(x), _ptr(y), ctypes.c_void_p(_stream(stream))), "om_spmv")
+    return y
+
+
+def ilu_apply(M: ILU, v: torch.Tensor, conj_transpose: bool = False, stream=None) -> torch.Tensor:
+    z = torch.empty_like(v)
+    check(_lib.load().om_ilu_apply(M.handle, 1 if conj_transpose else 0, _ptr(v.contiguous()), _ptr(z),
+                                   ctypes.c_void_p(_stream(stream))), "om_ilu_apply")
+    return z
+
+
+def observables(Nc: int, Nm: int, rho: torch.Tensor, stream=None):
+    """(<a^dag a>, <b^dag b>) of a CUDA rho."""
+    flat = rho.t().contiguous().view(-1) if rho.dim() == 2 else rho
+    out = (ctypes.c_double * 2)()
+    check(_lib.load().om_observables(int(Nc), int(Nm), _ptr(flat), ctypes.byref(out),
+                                     ctypes.c_void_p(_stream(stream))), "om_observables")
+    return out[0], out[1]

@@ -1,0 +1,76 @@
+// Status strings, per-thread error messages and small handle queries.
+#include <cstring>
+#include <string>
+
+#include "common.cuh"
+
+namespace omss {
+namespace {
+thread_local std::string g_last_error;
+}
+void set_error(const std::string &msg) { g_last_error = msg; }
+}  // namespace omss
+
+using namespace omss;
+
+extern "C" const char *om_status_str(om_status s) {
+    switch (s) {
+        case OM_OK: return "OM_OK";
+        case OM_EINVAL: return "OM_EINVAL: invalid argument";
+        case OM_ENOMEM: return "OM_ENOMEM: out of memory";
+        case OM_ECUDA: return "OM_ECUDA: CUDA runtime error";
+        case OM_EZEROPIVOT: return "OM_EZEROPIVOT: zero pivot in ILU";
+        case OM_ENOCONV: return "OM_ENOCONV: GMRES did not reach the tolerance";
+        case OM_EBREAKDOWN: return "OM_EBREAKDOWN: Arnoldi breakdown";
+        case OM_ENUMERIC: return "OM_ENUMERIC: NaN or Inf";
+        case OM_ETIMEOUT: return "OM_ETIMEOUT: device wait timed out";
+    }
+    return "unknown om_status";
+}
+
+extern "C" const char *om_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" om_status om_matrix_info(const om_matrix *A, int64_t *nrows, int64_t *nnz, double *w,
+                                    double *norm_inf) {
+    return guarded([&] {
+        OM_REQUIRE(A, "om_matrix_info: NULL matrix");
+        if (nrows) *nrows = A->N;
+        if (nnz) *nnz = A->nnz;
+        if (w) *w = A->w;
+        if (norm_inf) *norm_inf = A->norm_inf;
+    });
+}
+
+extern "C" om_status om_matrix_export(const om_matrix *A, int64_t *rowptr, int32_t *col, double *val,
+                                      void *stream) {
+    return guarded([&] {
+        OM_REQUIRE(A, "om_matrix_export: NULL matrix");
+        cudaStream_t s = as_stream(stream);
+        if (rowptr)
+            OM_CUDA_TRY(cudaMemcpyAsync(rowptr, A->rowptr.p, sizeof(int64_t) * (A->N + 1),
+                                        cudaMemcpyDeviceToHost, s));
+        if (col && A->nnz)
+            OM_CUDA_TRY(cudaMemcpyAsync(col, A->col.p, sizeof(int32_t) * A->nnz, cudaMemcpyDeviceToHost, s));
+        if (val && A->nnz)
+            OM_CUDA_TRY(cudaMemcpyAsync(val, A->val.p, sizeof(double2) * A->nnz, cudaMemcpyDeviceToHost, s));
+        OM_CUDA_TRY(cudaStreamSynchronize(s));
+    });
+}
+
+extern "C" void om_matrix_free(om_matrix *A) { delete A; }
+extern "C" void om_ilu_free(om_ilu *M) { delete M; }
+
+namespace omss {
+void csr_to_host(const om_matrix &A, std::vector<int64_t> &rp, std::vector<int32_t> &ci,
+                 std::vector<double2> &va, cudaStream_t s) {
+    rp.resize(A.N + 1);
+    ci.resize(A.nnz);
+    va.resize(A.nnz);
+    OM_CUDA_TRY(cudaMemcpyAsync(rp.data(), A.rowptr.p, sizeof(int64_t) * (A.N + 1), cudaMemcpyDeviceToHost, s));
+    if (A.nnz) {
+        OM_CUDA_TRY(cudaMemcpyAsync(ci.data(), A.col.p, sizeof(int32_t) * A.nnz, cudaMemcpyDeviceToHost, s));
+        OM_CUDA_TRY(cudaMemcpyAsync(va.data(), A.val.p, sizeof(double2) * A.nnz, cudaMemcpyDeviceToHost, s));
+    }
+    OM_CUDA_TRY(cudaStreamSynchronize(s));
+}
+}  // namespace omss

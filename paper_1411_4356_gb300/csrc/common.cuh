@@ -1,0 +1,189 @@
+// Internal declarations shared by the translation units of libomss.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "omss.h"
+
+// ---------------------------------------------------------------- errors
+namespace omss {
+
+void set_error(const std::string &msg);
+
+struct Error {
+    om_status status;
+    std::string msg;
+};
+
+#define OM_CUDA_TRY(expr)                                                                   \
+    do {                                                                                    \
+        cudaError_t _e = (expr);                                                            \
+        if (_e != cudaSuccess)                                                              \
+            throw ::omss::Error{_e == cudaErrorMemoryAllocation ? OM_ENOMEM : OM_ECUDA,    \
+                                std::string(#expr) + ": " + cudaGetErrorString(_e)};        \
+    } while (0)
+
+#define OM_REQUIRE(cond, msg)                                                               \
+    do {                                                                                    \
+        if (!(cond)) throw ::omss::Error{OM_EINVAL, std::string(msg)};                      \
+    } while (0)
+
+#define OM_CHECK_LAUNCH() OM_CUDA_TRY(cudaGetLastError())
+
+// Runs `body`, converting exceptions to om_status.
+template <class F>
+om_status guarded(F &&body) {
+    try {
+        body();
+        return OM_OK;
+    } catch (const Error &e) {
+        set_error(e.msg);
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        set_error("host allocation failed");
+        return OM_ENOMEM;
+    } catch (const std::exception &e) {
+        set_error(e.what());
+        return OM_EINVAL;
+    }
+}
+
+// ------------------------------------------------------- device buffers
+// Stream-ordered device allocation owned by a handle.
+template <class T>
+struct DBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    void alloc(size_t count, cudaStream_t s) {
+        release(s);
+        n = count;
+        if (count) OM_CUDA_TRY(cudaMallocAsync((void **)&p, sizeof(T) * count, s));
+    }
+    void release(cudaStream_t s) {
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline int num_sms() {
+    static int sms = [] {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 1;
+    }();
+    return sms;
+}
+
+// -------------------------------------------------------- complex helpers
+__host__ __device__ inline double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+__host__ __device__ inline double2 cmulc(double2 a, double2 b) {
+    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ inline double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__host__ __device__ inline double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ inline double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+
+__host__ __device__ inline float2 cmulf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline float2 cmulcf(float2 a, float2 b) {
+    return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+
+}  // namespace omss
+
+// ------------------------------------------------------------- handles
+// Complex CSR matrix on the device: int64 row pointers, int32 columns
+// (sorted within a row), c128 values.
+struct om_matrix {
+    int64_t N = 0;      // rows = columns
+    int64_t nnz = 0;
+    int32_t n = 0;      // Hilbert dimension Nc*Nm (N = n*n)
+    om_params params{};
+    int32_t trace_mode = 0;
+    double nth_eff = 0;  // n_th actually used (after the floor)
+    double w = 0;        // Eq. 5 weight
+    double norm_inf = 0; // ||L||_inf of the unmodified Liouvillian
+    bool permuted = false;
+    int64_t trace_row = 0;  // row index of the trace row (0, or its RCM position)
+    omss::DBuf<int64_t> rowptr;
+    omss::DBuf<int32_t> col;
+    omss::DBuf<double2> val;
+    // original row 0 of L (before the trace row was formed), columns in the
+    // numbering of this matrix; host copies (<= 16 entries)
+    std::vector<int32_t> row0_col;
+    std::vector<double2> row0_val;
+    omss::DBuf<int32_t> d_row0_col;
+    omss::DBuf<double2> d_row0_val;
+    // positions of the diagonal elements rho_ii in this matrix's numbering
+    omss::DBuf<int32_t> diag_pos;
+    cudaStream_t owner_stream = nullptr;
+    ~om_matrix();
+};
+
+// One triangular factor in CSR (strict part) plus optional inverse diagonal.
+struct om_tri {
+    int64_t N = 0, nnz = 0;
+    omss::DBuf<int64_t> rowptr;
+    omss::DBuf<int32_t> col;
+    omss::DBuf<double2> val;
+    omss::DBuf<float2> val32;     // complex64 copy (mixed precision)
+    int64_t levels = 0;           // depth of the dependency DAG
+    void release(cudaStream_t s) {
+        rowptr.release(s);
+        col.release(s);
+        val.release(s);
+        val32.release(s);
+    }
+};
+
+struct om_ilu {
+    int64_t N = 0;
+    om_tri L;        // strict lower part of the unit lower factor
+    om_tri U;        // strict upper part of U
+    omss::DBuf<double2> dinv;   // 1 / u_ii
+    omss::DBuf<double2> dinvh;  // 1 / conj(u_ii), diagonal of U^H inverted
+    omss::DBuf<float2> dinv32;
+    // conjugate transposes, stored as CSR of U^H (strict lower) and L^H (strict upper)
+    om_tri UH;
+    om_tri LH;
+    int64_t n_guarded = 0;
+    omss::DBuf<int> status;     // device status word for bounded waits
+    cudaStream_t owner_stream = nullptr;
+    ~om_ilu();
+};
+
+namespace omss {
+
+// Kernel launchers implemented in the .cu files.
+void spmv_c128(const int64_t *rowptr, const int32_t *col, const double2 *val, int64_t N,
+               const double2 *x, double2 *y, cudaStream_t s);
+void spmv_c64(const int64_t *rowptr, const int32_t *col, const float2 *val, int64_t N,
+              const float2 *x, float2 *y, cudaStream_t s);
+
+// z = T^{-1} v for a triangular factor; lower: forward rows 0..N-1, else
+// backward; dinv == nullptr means unit diagonal.  v and z may alias.
+void sweep_c128(const om_tri &T, bool lower, const double2 *dinv, const double2 *v, double2 *z,
+                int *status, int64_t timeout_ns, cudaStream_t s);
+void sweep_c64(const om_tri &T, bool lower, const float2 *dinv, const float2 *v, float2 *z,
+               int *status, int64_t timeout_ns, cudaStream_t s);
+
+// Host-side helpers (permute.cu / ilu.cu)
+void csr_to_host(const om_matrix &A, std::vector<int64_t> &rp, std::vector<int32_t> &ci,
+                 std::vector<double2> &va, cudaStream_t s);
+
+}  // namespace omss

@@ -1,0 +1,281 @@
+// Sec. II: ILUT(d, p), the dual-threshold incomplete LU factorisation used
+// as the preconditioner M = L U of Eq. 6, and the device layout of its
+// factors.
+//
+// Row-wise (i-k-j) elimination.  In row i every entry whose modulus falls
+// below d * ||row i of A||_inf is dropped, original entries included (Sec. IV:
+// the 1e-15 thermal entries are absent from the preconditioner); the diagonal
+// is kept.  The cap p * NNZ(A) is honoured row by row: the strict L part keeps
+// at most floor(p * nnz_i / 2) entries and the U part, diagonal included, at
+// most as many; the largest moduli win, ties go to the smaller column.  No
+// pivoting (after the reordering the diagonal of L~ is zero-free); a pivot
+// below 1e-14 ||row i||_inf is replaced by that value and counted.
+//
+// The factorisation runs on the host (it is the serial setup stage of the
+// method); the factors are then laid out on the device for the sweeps:
+// strict L, strict U and 1/u_ii in CSR (int64 row pointers, int32 columns,
+// c128 values), plus complex64 copies and the conjugate transposes U^H, L^H
+// used by the adjoint.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <memory>
+#include <queue>
+
+#include "common.cuh"
+
+namespace omss {
+namespace {
+
+using cd = std::complex<double>;
+
+struct HostTri {
+    std::vector<int64_t> rp;
+    std::vector<int32_t> ci;
+    std::vector<cd> va;
+};
+
+struct Picked {
+    int32_t c;
+    double mag;
+};
+
+void ilut_host(int64_t N, const std::vector<int64_t> &arp, const std::vector<int32_t> &aci,
+               const std::vector<double2> &ava, double droptol, double fill, bool compensate,
+               HostTri &L, HostTri &U, std::vector<cd> &diag, int64_t &guarded) {
+    std::vector<cd> w(N, cd(0, 0));
+    std::vector<char> in_row(N, 0);
+    std::vector<int32_t> present;
+    std::vector<Picked> lo, hi;
+    std::priority_queue<int32_t, std::vector<int32_t>, std::greater<int32_t>> pending;
+    L.rp.assign(N + 1, 0);
+    U.rp.assign(N + 1, 0);
+    diag.assign(N, cd(0, 0));
+    guarded = 0;
+    auto by_size = [](const Picked &a, const Picked &b) { return a.mag != b.mag ? a.mag > b.mag : a.c < b.c; };
+    for (int64_t i = 0; i < N; ++i) {
+        const int64_t nnz_i = arp[i + 1] - arp[i];
+        double anorm = 0;
+        for (int64_t e = arp[i]; e < arp[i + 1]; ++e) anorm = std::max(anorm, std::abs(cd(ava[e].x, ava[e].y)));
+        const double tau = droptol * anorm;
+        int64_t cap = (int64_t)std::floor(fill * (double)nnz_i / 2.0);
+        if (cap < 1) cap = 1;
+        present.clear();
+        for (int64_t e = arp[i]; e < arp[i + 1]; ++e) {
+            int32_t c = aci[e];
+            w[c] = cd(ava[e].x, ava[e].y);
+            in_row[c] = 1;
+            present.push_back(c);
+            if (c < i) pending.push(c);
+        }
+        if (!in_row[i]) {
+            in_row[i] = 1;
+            w[i] = 0;
+            present.push_back((int32_t)i);
+        }
+        double dropped = 0;
+        while (!pending.empty()) {
+            int32_t k = pending.top();
+            pending.pop();
+            cd m = w[k] / diag[k];
+            if (std::abs(m) < tau) {
+                dropped += std::abs(w[k]);
+                w[k] = 0;
+                continue;
+            }
+            w[k] = m;
+            for (int64_t e = U.rp[k]; e < U.rp[k + 1]; ++e) {
+                int32_t c = U.ci[e];
+                if (!in_row[c]) {
+                    in_row[c] = 1;
+                    w[c] = 0;
+                    present.push_back(c);
+                    if (c < i) pending.push(c);
+                }
+                w[c] -= m * U.va[e];
+            }
+        }
+        lo.clear();
+        hi.clear();
+        for (int32_t c : present) {
+            if (c == i) continue;
+            double mg = std::abs(w[c]);
+            bool keep = w[c] != cd(0, 0) && !(mg < tau);
+            if (c < i) {
+                if (keep) lo.push_back({c, mg});
+            } else {
+                if (keep) hi.push_back({c, mg});
+                else dropped += mg;
+            }
+        }
+        if ((int64_t)lo.size() > cap) {
+            std::nth_element(lo.begin(), lo.begin() + cap, lo.end(), by_size);
+            for (size_t t = cap; t < lo.size(); ++t) dropped += lo[t].mag * std::abs(diag[lo[t].c]);
+            lo.resize(cap);
+        }
+        if ((int64_t)hi.size() > cap - 1) {
+            std::nth_element(hi.begin(), hi.begin() + (cap - 1), hi.end(), by_size);
+            for (size_t t = cap - 1; t < hi.size(); ++t) dropped += hi[t].mag;
+            hi.resize(cap - 1);
+        }
+        auto by_col = [](const Picked &a, const Picked &b) { return a.c < b.c; };
+        std::sort(lo.begin(), lo.end(), by_col);
+        std::sort(hi.begin(), hi.end(), by_col);
+        for (auto &t : lo) {
+            L.ci.push_back(t.c);
+            L.va.push_back(w[t.c]);
+        }
+        L.rp[i + 1] = (int64_t)L.ci.size();
+        cd piv = w[i];
+        if (compensate && dropped > 0) piv = (std::abs(piv) > 0) ? piv + dropped * piv / std::abs(piv) : cd(dropped, 0);
+        const double floor_ = 1e-14 * anorm;
+        if (std::abs(piv) < floor_ || piv == cd(0, 0)) {
+            piv = cd(floor_ > 0 ? floor_ : 1e-300, 0);
+            ++guarded;
+        }
+        diag[i] = piv;
+        for (auto &t : hi) {
+            U.ci.push_back(t.c);
+            U.va.push_back(w[t.c]);
+        }
+        U.rp[i + 1] = (int64_t)U.ci.size();
+        for (int32_t c : present) {
+            w[c] = 0;
+            in_row[c] = 0;
+        }
+    }
+}
+
+// Conjugate transpose of a strict triangular CSR.
+HostTri conj_transpose(int64_t N, const HostTri &T) {
+    HostTri R;
+    R.rp.assign(N + 1, 0);
+    for (int32_t c : T.ci) R.rp[c + 1]++;
+    for (int64_t r = 0; r < N; ++r) R.rp[r + 1] += R.rp[r];
+    R.ci.resize(T.ci.size());
+    R.va.resize(T.va.size());
+    std::vector<int64_t> pos(R.rp.begin(), R.rp.end() - 1);
+    for (int64_t r = 0; r < N; ++r)
+        for (int64_t e = T.rp[r]; e < T.rp[r + 1]; ++e) {
+            int64_t d = pos[T.ci[e]]++;
+            R.ci[d] = (int32_t)r;
+            R.va[d] = std::conj(T.va[e]);
+        }
+    return R;
+}
+
+// Depth of the dependency DAG of a strict triangular factor.
+int64_t dag_depth(int64_t N, const HostTri &T, bool lower) {
+    std::vector<int32_t> lev(N, 0);
+    int64_t best = 0;
+    for (int64_t t = 0; t < N; ++t) {
+        int64_t r = lower ? t : N - 1 - t;
+        int32_t l = 0;
+        for (int64_t e = T.rp[r]; e < T.rp[r + 1]; ++e) l = std::max(l, lev[T.ci[e]] + 1);
+        lev[r] = l;
+        best = std::max<int64_t>(best, l);
+    }
+    return N ? best + 1 : 0;
+}
+
+void upload(om_tri &D, int64_t N, const HostTri &T, bool want32, cudaStream_t s) {
+    D.N = N;
+    D.nnz = (int64_t)T.ci.size();
+    D.rowptr.alloc(N + 1, s);
+    D.col.alloc(std::max<int64_t>(D.nnz, 1), s);
+    D.val.alloc(std::max<int64_t>(D.nnz, 1), s);
+    OM_CUDA_TRY(cudaMemcpyAsync(D.rowptr.p, T.rp.data(), sizeof(int64_t) * (N + 1), cudaMemcpyHostToDevice, s));
+    if (D.nnz) {
+        OM_CUDA_TRY(cudaMemcpyAsync(D.col.p, T.ci.data(), sizeof(int32_t) * D.nnz, cudaMemcpyHostToDevice, s));
+        static_assert(sizeof(cd) == sizeof(double2), "complex layout");
+        OM_CUDA_TRY(cudaMemcpyAsync(D.val.p, T.va.data(), sizeof(double2) * D.nnz, cudaMemcpyHostToDevice, s));
+    }
+    if (want32) {
+        std::vector<float2> v32(T.va.size());
+        for (size_t t = 0; t < T.va.size(); ++t) v32[t] = make_float2((float)T.va[t].real(), (float)T.va[t].imag());
+        D.val32.alloc(std::max<int64_t>(D.nnz, 1), s);
+        if (D.nnz)
+            OM_CUDA_TRY(cudaMemcpyAsync(D.val32.p, v32.data(), sizeof(float2) * D.nnz, cudaMemcpyHostToDevice, s));
+        OM_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+}
+
+}  // namespace
+}  // namespace omss
+
+using namespace omss;
+
+om_ilu::~om_ilu() {
+    cudaStream_t s = owner_stream;
+    L.release(s);
+    U.release(s);
+    UH.release(s);
+    LH.release(s);
+    dinv.release(s);
+    dinvh.release(s);
+    dinv32.release(s);
+    status.release(s);
+}
+
+extern "C" om_status om_ilu_factor(const om_matrix *A, double droptol, double fill, int32_t flags,
+                                   void *stream, om_ilu **out) {
+    return guarded([&] {
+        OM_REQUIRE(A && out, "om_ilu_factor: NULL argument");
+        OM_REQUIRE(droptol >= 0 && fill > 0, "om_ilu_factor: droptol >= 0 and fill > 0 required");
+        *out = nullptr;
+        cudaStream_t s = as_stream(stream);
+        std::vector<int64_t> rp;
+        std::vector<int32_t> ci;
+        std::vector<double2> va;
+        csr_to_host(*A, rp, ci, va, s);
+        const int64_t N = A->N;
+        HostTri L, U;
+        std::vector<cd> diag;
+        int64_t guarded_count = 0;
+        ilut_host(N, rp, ci, va, droptol, fill, (flags & 1) != 0, L, U, diag, guarded_count);
+        auto M = std::make_unique<om_ilu>();
+        M->owner_stream = s;
+        M->N = N;
+        M->n_guarded = guarded_count;
+        upload(M->L, N, L, true, s);
+        upload(M->U, N, U, true, s);
+        M->L.levels = dag_depth(N, L, true);
+        M->U.levels = dag_depth(N, U, false);
+        HostTri UH = conj_transpose(N, U), LH = conj_transpose(N, L);
+        upload(M->UH, N, UH, false, s);
+        upload(M->LH, N, LH, false, s);
+        M->UH.levels = M->U.levels;
+        M->LH.levels = M->L.levels;
+        std::vector<double2> dinv(N);
+        std::vector<double2> dinvh(N);
+        std::vector<float2> dinv32(N);
+        for (int64_t i = 0; i < N; ++i) {
+            cd r = 1.0 / diag[i];
+            dinv[i] = make_double2(r.real(), r.imag());
+            dinvh[i] = make_double2(r.real(), -r.imag());
+            dinv32[i] = make_float2((float)r.real(), (float)r.imag());
+        }
+        M->dinv.alloc(N, s);
+        M->dinv32.alloc(N, s);
+        M->dinvh.alloc(N, s);
+        OM_CUDA_TRY(cudaMemcpyAsync(M->dinvh.p, dinvh.data(), sizeof(double2) * N, cudaMemcpyHostToDevice, s));
+        OM_CUDA_TRY(cudaMemcpyAsync(M->dinv.p, dinv.data(), sizeof(double2) * N, cudaMemcpyHostToDevice, s));
+        OM_CUDA_TRY(cudaMemcpyAsync(M->dinv32.p, dinv32.data(), sizeof(float2) * N, cudaMemcpyHostToDevice, s));
+        M->status.alloc(4, s);
+        OM_CUDA_TRY(cudaMemsetAsync(M->status.p, 0, sizeof(int) * 4, s));
+        OM_CUDA_TRY(cudaStreamSynchronize(s));
+        *out = M.release();
+    });
+}
+
+extern "C" om_status om_ilu_info(const om_ilu *M, int64_t *nnz_l, int64_t *nnz_u, int64_t *n_guarded,
+                                 int64_t *levels_l, int64_t *levels_u) {
+    return guarded([&] {
+        OM_REQUIRE(M, "om_ilu_info: NULL handle");
+        if (nnz_l) *nnz_l = M->L.nnz;
+        if (nnz_u) *nnz_u = M->U.nnz + M->N;  // diagonal of U included
+        if (n_guarded) *n_guarded = M->n_guarded;
+        if (levels_l) *levels_l = M->L.levels;
+        if (levels_u) *levels_u = M->U.levels;
+    });
+}

@@ -1,0 +1,255 @@
+// Sec. IV: the steady-state solve.  Restarted GMRES(m) on the permuted
+// trace-augmented system L~_rcm x = P (w, 0, ...)^T with right
+// preconditioning by the ILUT factors (Eq. 6 solves the same system with
+// the preconditioner on the left).  The stopping test is the normwise
+// backward error of the unmodified Liouvillian,
+//   eta = ||L x||_inf / (||L||_inf ||x||_inf),
+// evaluated in FP64 at the end of every cycle; then x is divided by its
+// trace (Tr rho = 1) and scattered back to natural order, giving the
+// column-stacked rho of Eq. 4.
+#include <chrono>
+#include <cmath>
+
+#include "krylov.cuh"
+
+namespace omss {
+namespace {
+
+__global__ void set_entry(double2 *b, int64_t pos, double2 v) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) b[pos] = v;
+}
+
+// y[trace_row] = (row 0 of the unmodified L) . x  (eta uses L, not L~)
+__global__ void fix_trace_row(double2 *y, const double2 *x, int64_t trace_row, const int32_t *c, const double2 *v,
+                              int cnt) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double2 s = make_double2(0, 0);
+    for (int t = 0; t < cnt; ++t) s = cadd(s, cmul(v[t], x[c[t]]));
+    y[trace_row] = s;
+}
+
+// out = sum_i x[pos[i]] over i < n (fixed order within a single block)
+__global__ void gather_sum(const double2 *x, const int32_t *pos, int n, double2 *out) {
+    __shared__ double2 red[256];
+    double2 s = make_double2(0, 0);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s = cadd(s, x[pos[i]]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double2 t = make_double2(0, 0);
+        for (int q = 0; q < (int)blockDim.x; ++q) t = cadd(t, red[q]);
+        out[0] = t;
+    }
+}
+
+// rho[perm[r]] = x[r] / t
+__global__ void normalise_scatter(const double2 *__restrict__ x, const int32_t *__restrict__ perm, int64_t N,
+                                  const double2 *t, double2 *__restrict__ rho) {
+    const double2 tt = t[0];
+    const double d = cabs2(tt);
+    const double2 inv = make_double2(tt.x / d, -tt.y / d);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N; r += stride)
+        rho[perm[r]] = cmul(x[r], inv);
+}
+
+// <a^dag a> = sum_h c(h) rho_hh, <b^dag b> = sum_h m(h) rho_hh
+__global__ void observables_kernel(int Nc, int Nm, const double2 *rho, double *out) {
+    __shared__ double ra[256], rb[256];
+    const int n = Nc * Nm;
+    double sa = 0, sb = 0;
+    for (int h = threadIdx.x; h < n; h += blockDim.x) {
+        double p = rho[(int64_t)h * (n + 1)].x;
+        sa += (h / Nm) * p;
+        sb += (h % Nm) * p;
+    }
+    ra[threadIdx.x] = sa;
+    rb[threadIdx.x] = sb;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0, tb = 0;
+        for (int q = 0; q < (int)blockDim.x; ++q) {
+            ta += ra[q];
+            tb += rb[q];
+        }
+        out[0] = ta;
+        out[1] = tb;
+    }
+}
+
+struct ForwardOps : KrylovOps {
+    const om_matrix *A;
+    const om_ilu *M;
+    int64_t timeout;
+    void apply(const double2 *v, double2 *out, cudaStream_t s) override {
+        spmv_c128(A->rowptr.p, A->col.p, A->val.p, A->N, v, out, s);
+    }
+    void precond(const double2 *v, double2 *out, cudaStream_t s) override {
+        sweep_c128(M->L, true, nullptr, v, out, M->status.p, timeout, s);
+        sweep_c128(M->U, false, M->dinv.p, out, out, M->status.p, timeout, s);
+    }
+};
+
+}  // namespace
+
+// eta of x for the unmodified Liouvillian; y is scratch of length N
+double eta_of(const om_matrix &A, const double2 *x, double2 *y, GmresWork &W, cudaStream_t s) {
+    spmv_c128(A.rowptr.p, A.col.p, A.val.p, A.N, x, y, s);
+    fix_trace_row<<<1, 1, 0, s>>>(y, x, A.trace_row, A.d_row0_col.p, A.d_row0_val.p, (int)A.row0_col.size());
+    OM_CHECK_LAUNCH();
+    double ly = dev_maxabs(y, A.N, W, s);
+    double lx = dev_maxabs(x, A.N, W, s);
+    return ly / (A.norm_inf * lx);
+}
+
+double2 trace_of(const om_matrix &A, const double2 *x, GmresWork &W, cudaStream_t s) {
+    double2 *t = reinterpret_cast<double2 *>(W.scal.p + 4);
+    gather_sum<<<1, 256, 0, s>>>(x, A.diag_pos.p, A.n, t);
+    OM_CHECK_LAUNCH();
+    double2 h;
+    OM_CUDA_TRY(cudaMemcpyAsync(&h, t, sizeof(double2), cudaMemcpyDeviceToHost, s));
+    OM_CUDA_TRY(cudaStreamSynchronize(s));
+    return h;
+}
+
+void normalise_into_rho(const om_matrix &A, const double2 *x, const int32_t *perm, double2 *rho, GmresWork &W,
+                        cudaStream_t s) {
+    double2 *t = reinterpret_cast<double2 *>(W.scal.p + 4);
+    gather_sum<<<1, 256, 0, s>>>(x, A.diag_pos.p, A.n, t);
+    int64_t need = (A.N + 255) / 256;
+    unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 4));
+    normalise_scatter<<<blocks, 256, 0, s>>>(x, perm, A.N, t, rho);
+    OM_CHECK_LAUNCH();
+}
+
+}  // namespace omss
+
+using namespace omss;
+
+static void check_solve_args(const om_matrix *A, const om_ilu *M, const int32_t *perm, const om_solve_opts *o) {
+    OM_REQUIRE(A && M && perm && o, "NULL argument");
+    OM_REQUIRE(A->permuted, "the matrix must come from om_permute");
+    OM_REQUIRE(M->N == A->N, "ILU and matrix sizes differ");
+    OM_REQUIRE(o->restart >= 1 && o->restart <= 120, "restart must be in [1, 120]");
+    OM_REQUIRE(o->max_iters >= 1, "max_iters must be >= 1");
+    OM_REQUIRE(o->tol > 0, "tol must be positive");
+    OM_REQUIRE(o->precision == 0 || o->precision == 1, "precision must be 0 or 1");
+}
+
+namespace omss {
+om_status solve_mixed(const om_matrix *A, const om_ilu *M, const int32_t *perm_dev, const om_solve_opts *opts,
+                      const double *x0, double *rho_dev, om_solve_info *info, void *stream);
+}
+
+extern "C" om_status om_steady_state_solve(const om_matrix *A, const om_ilu *M, const int32_t *perm_dev,
+                                           const om_solve_opts *opts, const double *x0, double *rho_dev,
+                                           om_solve_info *info, void *stream) {
+    if (opts && opts->precision == 1) return solve_mixed(A, M, perm_dev, opts, x0, rho_dev, info, stream);
+    om_status final_status = OM_OK;
+    om_status st = guarded([&] {
+        check_solve_args(A, M, perm_dev, opts);
+        OM_REQUIRE(rho_dev, "rho_dev is NULL");
+        auto t0 = std::chrono::steady_clock::now();
+        cudaStream_t s = as_stream(stream);
+        const int64_t N = A->N;
+        GmresWork W;
+        W.alloc(N, opts->restart, s);
+        DBuf<double2> b, x;
+        b.alloc(N, s);
+        x.alloc(N, s);
+        dev_zero(b.p, N, s);
+        set_entry<<<1, 1, 0, s>>>(b.p, A->trace_row, make_double2(A->w, 0));
+        OM_CHECK_LAUNCH();
+        if (x0) dev_copy(reinterpret_cast<const double2 *>(x0), x.p, N, s);
+        else dev_zero(x.p, N, s);
+        OM_CUDA_TRY(cudaMemsetAsync(M->status.p, 0, sizeof(int), s));
+        ForwardOps ops;
+        ops.A = A;
+        ops.M = M;
+        ops.timeout = opts->wait_timeout_ns;
+        om_solve_info inf{};
+        double xinf = 1.0 / A->n;
+        double eta = INFINITY;
+        int its = 0, cycles = 0;
+        while (true) {
+            double target = 0.5 * opts->tol * A->norm_inf * xinf;
+            GmresResult r = gmres_cycle(ops, b.p, x.p, target, opts->max_iters - its, W, s);
+            its += r.iterations;
+            ++cycles;
+            eta = eta_of(*A, x.p, W.w.p, W, s);
+            xinf = dev_maxabs(x.p, N, W, s);
+            if (cycles <= 64) inf.residual_history[cycles - 1] = eta;
+            int timed_out = 0;
+            OM_CUDA_TRY(cudaMemcpyAsync(&timed_out, M->status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+            OM_CUDA_TRY(cudaStreamSynchronize(s));
+            if (timed_out) {
+                final_status = OM_ETIMEOUT;
+                break;
+            }
+            if (!std::isfinite(eta)) {
+                final_status = OM_ENUMERIC;
+                break;
+            }
+            if (eta <= opts->tol) break;
+            if (r.breakdown) {
+                final_status = OM_EBREAKDOWN;
+                break;
+            }
+            if (its >= opts->max_iters) {
+                final_status = OM_ENOCONV;
+                break;
+            }
+            if (r.iterations == 0) {  // residual already zero in FP64
+                break;
+            }
+        }
+        double2 tr = trace_of(*A, x.p, W, s);
+        normalise_into_rho(*A, x.p, perm_dev, reinterpret_cast<double2 *>(rho_dev), W, s);
+        OM_CUDA_TRY(cudaStreamSynchronize(s));
+        inf.iterations = its;
+        inf.cycles = cycles;
+        inf.eta = eta;
+        inf.trace_before = tr.x;
+        inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (info) *info = inf;
+        W.release(s);
+        b.release(s);
+        x.release(s);
+    });
+    return st != OM_OK ? st : final_status;
+}
+
+extern "C" om_status om_ilu_apply(const om_ilu *M, int32_t conj_transpose, const double *v, double *z, void *stream) {
+    return guarded([&] {
+        OM_REQUIRE(M && v && z, "om_ilu_apply: NULL argument");
+        cudaStream_t s = as_stream(stream);
+        const double2 *vv = reinterpret_cast<const double2 *>(v);
+        double2 *zz = reinterpret_cast<double2 *>(z);
+        OM_CUDA_TRY(cudaMemsetAsync(M->status.p, 0, sizeof(int), s));
+        if (!conj_transpose) {
+            sweep_c128(M->L, true, nullptr, vv, zz, M->status.p, 0, s);
+            sweep_c128(M->U, false, M->dinv.p, zz, zz, M->status.p, 0, s);
+        } else {
+            sweep_c128(M->UH, true, M->dinvh.p, vv, zz, M->status.p, 0, s);
+            sweep_c128(M->LH, false, nullptr, zz, zz, M->status.p, 0, s);
+        }
+        int flag = 0;
+        OM_CUDA_TRY(cudaMemcpyAsync(&flag, M->status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        OM_CUDA_TRY(cudaStreamSynchronize(s));
+        if (flag) throw Error{OM_ETIMEOUT, "triangular sweep wait timed out"};
+    });
+}
+
+extern "C" om_status om_observables(int32_t Nc, int32_t Nm, const double *rho_dev, double out[2], void *stream) {
+    return guarded([&] {
+        OM_REQUIRE(rho_dev && out && Nc >= 1 && Nm >= 1, "om_observables: bad argument");
+        cudaStream_t s = as_stream(stream);
+        DBuf<double> d;
+        d.alloc(2, s);
+        observables_kernel<<<1, 256, 0, s>>>(Nc, Nm, reinterpret_cast<const double2 *>(rho_dev), d.p);
+        OM_CHECK_LAUNCH();
+        OM_CUDA_TRY(cudaMemcpyAsync(out, d.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        OM_CUDA_TRY(cudaStreamSynchronize(s));
+        d.release(s);
+    });
+}
