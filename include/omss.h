@@ -76,7 +76,10 @@ typedef struct {
     int32_t precision;      /* 0: complex128 throughout;
                                1: complex64 inner GMRES / ILU / SpMV inside an
                                   FP64 iterative-refinement loop */
-    int32_t reserved;
+    int32_t precond_fp64;   /* 0: triangular sweeps with the complex64 copy of the
+                               factors (default: GB300's FP64 pipe runs at 1/64 of
+                               FP32, and the ILU is an approximation far coarser
+                               than FP32 rounding); 1: complex128 sweeps */
     double tol;             /* target of eta = ||L x||_inf / (||L||_inf ||x||_inf) */
     int64_t wait_timeout_ns;/* bound on any device spin-wait (0: 2 s default) */
 } om_solve_opts;
@@ -166,9 +169,10 @@ om_status om_steady_state_adjoint(const om_matrix *A_rcm, const om_ilu *M, const
 /* ---- single kernels, exposed for parity tests -------------------------------
  * y = A x (DEVICE c128 vectors of length nrows). */
 om_status om_spmv(const om_matrix *A, const double *x, double *y, void *stream);
-/* z = (L U)^{-1} v, or (L U)^{-H} v when conj_transpose != 0 (DEVICE c128[N]).
- * z and v may alias. */
-om_status om_ilu_apply(const om_ilu *M, int32_t conj_transpose, const double *v, double *z,
+/* z = (L U)^{-1} v, or (L U)^{-H} v, with DEVICE c128[N] vectors (z and v may
+ * alias).  flags bit 0: sweep with the complex128 factors (else complex64);
+ * bit 1: apply the conjugate transpose.  Errors: OM_EINVAL, OM_ETIMEOUT. */
+om_status om_ilu_apply(const om_ilu *M, int32_t flags, const double *v, double *z,
                        void *stream);
 /* <a^dag a>, <b^dag b> of a DEVICE rho (c128 n x n column-major); out HOST double[2]. */
 om_status om_observables(int32_t Nc, int32_t Nm, const double *rho_dev, double out[2],

@@ -23,7 +23,7 @@ class om_build_opts(ctypes.Structure):
 
 
 class om_solve_opts(ctypes.Structure):
-    _fields_ = [("restart", c_i32), ("max_iters", c_i32), ("precision", c_i32), ("reserved", c_i32),
+    _fields_ = [("restart", c_i32), ("max_iters", c_i32), ("precision", c_i32), ("precond_fp64", c_i32),
                 ("tol", c_dbl), ("wait_timeout_ns", c_i64)]
 
 

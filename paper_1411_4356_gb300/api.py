@@ -142,14 +142,15 @@ class SolveInfo:
     status: int
 
 
-def _opts(restart, max_iters, tol, precision, wait_timeout_ns):
-    return om_solve_opts(int(restart), int(max_iters), int(precision), 0, float(tol), int(wait_timeout_ns))
+def _opts(restart, max_iters, tol, precision, wait_timeout_ns, precond_fp64=False):
+    return om_solve_opts(int(restart), int(max_iters), int(precision), 1 if precond_fp64 else 0, float(tol),
+                         int(wait_timeout_ns))
 
 
 def steady_state_solve(A_rcm: Matrix, M: ILU, perm: torch.Tensor, restart: int = 30, max_iters: int = 5000,
                        tol: float = 1e-10, precision: int = 0, x0: torch.Tensor | None = None,
                        wait_timeout_ns: int = 0, stream=None, raise_on_noconv: bool = True,
-                       rho_out: torch.Tensor | None = None):
+                       rho_out: torch.Tensor | None = None, precond_fp64: bool = False):
     """Sec. IV: rho (n x n complex128 CUDA tensor, rho[i, j] = rho_ij) and SolveInfo."""
     lib = _lib.load()
     n = A_rcm.params.Nc * A_rcm.params.Nm
@@ -158,7 +159,7 @@ def steady_state_solve(A_rcm: Matrix, M: ILU, perm: torch.Tensor, restart: int =
     _require_cuda(flat, torch.complex128, n * n, "rho_out")
     if x0 is not None:
         _require_cuda(x0, torch.complex128, A_rcm.N, "x0")
-    o = _opts(restart, max_iters, tol, precision, wait_timeout_ns)
+    o = _opts(restart, max_iters, tol, precision, wait_timeout_ns, precond_fp64)
     info = om_solve_info()
     st = lib.om_steady_state_solve(A_rcm.handle, M.handle, _ptr(perm), ctypes.byref(o), _ptr(x0), _ptr(flat),
                                    ctypes.byref(info), ctypes.c_void_p(_stream(stream)))
@@ -197,9 +198,12 @@ def spmv(A: Matrix, x: torch.Tensor, stream=None) -> torch.Tensor:
     return y
 
 
-def ilu_apply(M: ILU, v: torch.Tensor, conj_transpose: bool = False, stream=None) -> torch.Tensor:
+def ilu_apply(M: ILU, v: torch.Tensor, conj_transpose: bool = False, fp64: bool = False,
+              stream=None) -> torch.Tensor:
+    """z = (L U)^{-1} v (or (L U)^{-H} v); fp64 selects the complex128 sweeps."""
     z = torch.empty_like(v)
-    check(_lib.load().om_ilu_apply(M.handle, 1 if conj_transpose else 0, _ptr(v.contiguous()), _ptr(z),
+    flags = (1 if fp64 else 0) | (2 if conj_transpose else 0)
+    check(_lib.load().om_ilu_apply(M.handle, flags, _ptr(v.contiguous()), _ptr(z),
                                    ctypes.c_void_p(_stream(stream))), "om_ilu_apply")
     return z
 

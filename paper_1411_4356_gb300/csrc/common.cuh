@@ -158,6 +158,7 @@ struct om_ilu {
     omss::DBuf<double2> dinv;   // 1 / u_ii
     omss::DBuf<double2> dinvh;  // 1 / conj(u_ii), diagonal of U^H inverted
     omss::DBuf<float2> dinv32;
+    omss::DBuf<float2> dinvh32;
     // conjugate transposes, stored as CSR of U^H (strict lower) and L^H (strict upper)
     om_tri UH;
     om_tri LH;
@@ -181,6 +182,13 @@ void sweep_c128(const om_tri &T, bool lower, const double2 *dinv, const double2 
                 int *status, int64_t timeout_ns, cudaStream_t s);
 void sweep_c64(const om_tri &T, bool lower, const float2 *dinv, const float2 *v, float2 *z,
                int *status, int64_t timeout_ns, cudaStream_t s);
+
+// z = M^{-1} v (or M^{-H} v) with complex128 vectors; fp64 selects complex128
+// sweeps, otherwise the complex64 factors are used through tmp32 (N entries).
+void precond_apply(const om_ilu &M, bool conj_transpose, bool fp64, const double2 *v, double2 *z,
+                   float2 *tmp32, int64_t timeout_ns, cudaStream_t s);
+void to_c64(const double2 *v, int64_t N, float2 *out, cudaStream_t s);
+void to_c128(const float2 *v, int64_t N, double2 *out, cudaStream_t s);
 
 // Host-side helpers (permute.cu / ilu.cu)
 void csr_to_host(const om_matrix &A, std::vector<int64_t> &rp, std::vector<int32_t> &ci,

@@ -214,6 +214,7 @@ om_ilu::~om_ilu() {
     dinv.release(s);
     dinvh.release(s);
     dinv32.release(s);
+    dinvh32.release(s);
     status.release(s);
 }
 
@@ -242,22 +243,25 @@ extern "C" om_status om_ilu_factor(const om_matrix *A, double droptol, double fi
         M->L.levels = dag_depth(N, L, true);
         M->U.levels = dag_depth(N, U, false);
         HostTri UH = conj_transpose(N, U), LH = conj_transpose(N, L);
-        upload(M->UH, N, UH, false, s);
-        upload(M->LH, N, LH, false, s);
+        upload(M->UH, N, UH, true, s);
+        upload(M->LH, N, LH, true, s);
         M->UH.levels = M->U.levels;
         M->LH.levels = M->L.levels;
         std::vector<double2> dinv(N);
         std::vector<double2> dinvh(N);
-        std::vector<float2> dinv32(N);
+        std::vector<float2> dinv32(N), dinvh32(N);
         for (int64_t i = 0; i < N; ++i) {
             cd r = 1.0 / diag[i];
             dinv[i] = make_double2(r.real(), r.imag());
             dinvh[i] = make_double2(r.real(), -r.imag());
             dinv32[i] = make_float2((float)r.real(), (float)r.imag());
+            dinvh32[i] = make_float2((float)r.real(), -(float)r.imag());
         }
         M->dinv.alloc(N, s);
         M->dinv32.alloc(N, s);
         M->dinvh.alloc(N, s);
+        M->dinvh32.alloc(N, s);
+        OM_CUDA_TRY(cudaMemcpyAsync(M->dinvh32.p, dinvh32.data(), sizeof(float2) * N, cudaMemcpyHostToDevice, s));
         OM_CUDA_TRY(cudaMemcpyAsync(M->dinvh.p, dinvh.data(), sizeof(double2) * N, cudaMemcpyHostToDevice, s));
         OM_CUDA_TRY(cudaMemcpyAsync(M->dinv.p, dinv.data(), sizeof(double2) * N, cudaMemcpyHostToDevice, s));
         OM_CUDA_TRY(cudaMemcpyAsync(M->dinv32.p, dinv32.data(), sizeof(float2) * N, cudaMemcpyHostToDevice, s));

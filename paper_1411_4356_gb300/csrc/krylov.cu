@@ -1,5 +1,5 @@
 // K8 / K9: the Arnoldi process and the Givens least-squares update of
-// restarted GMRES (Sec. IV), right-preconditioned.
+// restarted GMRES (Sec. IV), right-preconditioned in its flexible form.
 //
 // Per inner step j the basis is extended with classical Gram-Schmidt applied
 // twice (CGS2): h = V^H w and w -= V h, repeated once, in fused multi-dot and
@@ -247,6 +247,8 @@ void GmresWork::alloc(int64_t n_, int m_, cudaStream_t s) {
     N = n_;
     m = m_;
     V.alloc((size_t)(m + 1) * N, s);
+    Z.alloc((size_t)m * N, s);
+    tmp32.alloc(N, s);
     w.alloc(N, s);
     z.alloc(N, s);
     r.alloc(N, s);
@@ -262,6 +264,8 @@ void GmresWork::alloc(int64_t n_, int m_, cudaStream_t s) {
 
 void GmresWork::release(cudaStream_t s) {
     V.release(s);
+    Z.release(s);
+    tmp32.release(s);
     w.release(s);
     z.release(s);
     r.release(s);
@@ -341,8 +345,9 @@ GmresResult gmres_cycle(KrylovOps &ops, const double2 *b, double2 *x, double tar
     for (int j = 0; j < m && res.iterations < max_iters; ++j) {
         double2 *vj = W.V.p + (int64_t)j * N;
         double2 *vnext = W.V.p + (int64_t)(j + 1) * N;
-        ops.precond(vj, W.z.p, s);
-        ops.apply(W.z.p, W.w.p, s);
+        double2 *zj = W.Z.p + (int64_t)j * N;
+        ops.precond(vj, zj, s);
+        ops.apply(zj, W.w.p, s);
         // CGS2
         for (int pass = 0; pass < 2; ++pass) {
             for (int f = 0; f <= j; f += kChunk) {
@@ -379,10 +384,9 @@ GmresResult gmres_cycle(KrylovOps &ops, const double2 *b, double2 *x, double tar
     res.last_estimate = est;
     if (k > 0) {
         back_substitute<<<1, 1, 0, s>>>(W.H.p, m + 1, W.g.p, k, W.y.p);
-        combine<<<grid_for(N), kThreads, 0, s>>>(W.V.p, N, k, W.y.p, W.w.p);
+        combine<<<grid_for(N), kThreads, 0, s>>>(W.Z.p, N, k, W.y.p, W.w.p);
         OM_CHECK_LAUNCH();
-        ops.precond(W.w.p, W.z.p, s);
-        dev_axpby(make_double2(1, 0), W.z.p, make_double2(1, 0), x, N, s);
+        dev_axpby(make_double2(1, 0), W.w.p, make_double2(1, 0), x, N, s);
     }
     res.cycles = 1;
     return res;

@@ -16,6 +16,8 @@ struct GmresWork {
     int64_t N = 0;
     int m = 0;
     DBuf<double2> V;        // (m+1) x N basis
+    DBuf<double2> Z;        // m x N preconditioned basis (flexible GMRES)
+    DBuf<float2> tmp32;     // complex64 work vector for the sweeps
     DBuf<double2> w, z, r;  // work vectors
     DBuf<double2> partial;  // per-block dot partials
     DBuf<double2> h;        // current Hessenberg column (m+2)
@@ -33,7 +35,9 @@ struct GmresResult {
     bool breakdown = false;
 };
 
-// Restarted right-preconditioned GMRES(m) on ops, x updated in place.
+// One cycle of flexible (right-preconditioned) GMRES(m): z_j = M^{-1} v_j is
+// stored, so x += Z y stays exact even when M^{-1} is applied in lower
+// precision.  x is updated in place.
 // `target` bounds ||b - A x||_2 for the inner iterations of one cycle.
 // Returns after one cycle.
 GmresResult gmres_cycle(KrylovOps &ops, const double2 *b, double2 *x, double target, int max_iters,

@@ -81,12 +81,13 @@ struct ForwardOps : KrylovOps {
     const om_matrix *A;
     const om_ilu *M;
     int64_t timeout;
+    bool fp64_precond;
+    float2 *tmp32;
     void apply(const double2 *v, double2 *out, cudaStream_t s) override {
         spmv_c128(A->rowptr.p, A->col.p, A->val.p, A->N, v, out, s);
     }
     void precond(const double2 *v, double2 *out, cudaStream_t s) override {
-        sweep_c128(M->L, true, nullptr, v, out, M->status.p, timeout, s);
-        sweep_c128(M->U, false, M->dinv.p, out, out, M->status.p, timeout, s);
+        precond_apply(*M, false, fp64_precond, v, out, tmp32, timeout, s);
     }
 };
 
@@ -167,6 +168,8 @@ extern "C" om_status om_steady_state_solve(const om_matrix *A, const om_ilu *M, 
         ops.A = A;
         ops.M = M;
         ops.timeout = opts->wait_timeout_ns;
+        ops.fp64_precond = opts->precond_fp64 != 0;
+        ops.tmp32 = W.tmp32.p;
         om_solve_info inf{};
         double xinf = 1.0 / A->n;
         double eta = INFINITY;
@@ -219,20 +222,18 @@ extern "C" om_status om_steady_state_solve(const om_matrix *A, const om_ilu *M, 
     return st != OM_OK ? st : final_status;
 }
 
-extern "C" om_status om_ilu_apply(const om_ilu *M, int32_t conj_transpose, const double *v, double *z, void *stream) {
+extern "C" om_status om_ilu_apply(const om_ilu *M, int32_t flags, const double *v, double *z, void *stream) {
+    const int32_t conj_transpose = flags & 2 ? 1 : 0;
     return guarded([&] {
         OM_REQUIRE(M && v && z, "om_ilu_apply: NULL argument");
         cudaStream_t s = as_stream(stream);
         const double2 *vv = reinterpret_cast<const double2 *>(v);
         double2 *zz = reinterpret_cast<double2 *>(z);
         OM_CUDA_TRY(cudaMemsetAsync(M->status.p, 0, sizeof(int), s));
-        if (!conj_transpose) {
-            sweep_c128(M->L, true, nullptr, vv, zz, M->status.p, 0, s);
-            sweep_c128(M->U, false, M->dinv.p, zz, zz, M->status.p, 0, s);
-        } else {
-            sweep_c128(M->UH, true, M->dinvh.p, vv, zz, M->status.p, 0, s);
-            sweep_c128(M->LH, false, nullptr, zz, zz, M->status.p, 0, s);
-        }
+        DBuf<float2> tmp;
+        tmp.alloc(M->N, s);
+        precond_apply(*M, conj_transpose != 0, (flags & 1) != 0, vv, zz, tmp.p, 0, s);
+        tmp.release(s);
         int flag = 0;
         OM_CUDA_TRY(cudaMemcpyAsync(&flag, M->status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         OM_CUDA_TRY(cudaStreamSynchronize(s));

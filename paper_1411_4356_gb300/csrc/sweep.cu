@@ -7,27 +7,37 @@
 // sweep across the whole GPU would spend a grid-wide barrier per level.  This
 // sweep instead keeps the whole dependency chain inside ONE thread block:
 //
-//  * 32 warps take rows in order, warp w owning rows t = w, w + 32, ...
+//  * 16 warps take rows in order, warp w owning rows t = w, w + 16, ...
 //    (t counts rows in sweep order: t = r for a forward sweep, t = N-1-r for
 //    a backward one);
-//  * a warp works on one row at a time, its lanes striding over the row's
-//    entries; each lane waits (in shared memory) until the row it needs is
-//    done, so a dependency hop costs a shared-memory flag round trip rather
-//    than an L2 round trip;
+//  * a warp works on one row at a time: it first loads the whole row (up to
+//    512 entries, 16 per lane, in registers) together with v_r and 1/u_rr,
+//    so that no memory latency sits between a dependency becoming ready and
+//    the row finishing; then each lane waits (in shared memory) for the rows
+//    its entries need, so a dependency hop costs a shared-memory flag round
+//    trip rather than an L2 round trip;
 //  * finished values go to a ring buffer of WIN rows in shared memory (the
 //    RCM band keeps most dependencies inside it) and to global memory; values
-//    older than WIN - SLACK rows are read back from L2;
+//    older than WIN - SLACK rows are read back from L2 once the owning warp
+//    has published them with a device-scope fence (every 32 of its rows, so
+//    the fence stays off the dependency chain);
+//  * the ring value is stored before the progress flag with volatile
+//    shared-memory accesses, which a warp performs in program order, so a
+//    reader needs no fence between seeing the flag and reading the value;
 //  * a warp may not start row t before every warp has reached row
 //    t - SLACK, so that ring slots are never overwritten while still needed;
 //  * every wait is bounded: after timeout_ns of spinning the status word is
 //    set, the abort flag releases every other wait, and the kernel winds
 //    down writing NaN.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace omss {
 namespace {
 
-constexpr int kWarps = 32;
+constexpr int kWarps = 16;   // warps of the single block
+constexpr int kRegs = 16;    // entries per lane held in registers (rows up to 512 entries)
 constexpr int kSlack = 1024;
 
 __device__ inline uint64_t global_ns() {
@@ -91,11 +101,13 @@ sweep_one_block(int64_t N, const int64_t *__restrict__ rp, const int32_t *__rest
     CT *win = reinterpret_cast<CT *>(smem_raw);
     __shared__ volatile int64_t progress[kWarps];  // last finished t of each warp
     __shared__ volatile int64_t current[kWarps];   // t each warp is on (or will start next)
+    __shared__ volatile int64_t committed[kWarps]; // last t whose global store is device-visible
     __shared__ volatile int abort_flag;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) {
         progress[warp] = -1;
         current[warp] = warp;
+        committed[warp] = -1;
     }
     if (threadIdx.x == 0) abort_flag = 0;
     __syncthreads();
@@ -103,13 +115,16 @@ sweep_one_block(int64_t N, const int64_t *__restrict__ rp, const int32_t *__rest
 
     for (int64_t t = warp; t < N; t += kWarps) {
         const int64_t r = LOWER ? t : N - 1 - t;
+        const int64_t b = rp[r], e = rp[r + 1];
+        const CT vr = ldcg(v + r);
+        const CT dr = dinv ? dinv[r] : O::zero();
         // throttle: every warp must have reached t - kSlack (warp-uniform decision)
         if (lane == 0) current[warp] = t;
         {
             int spins = 0;
             uint64_t since = 0;
             for (;;) {
-                int64_t c = current[lane];
+                int64_t c = lane < kWarps ? current[lane] : INT64_MAX;
                 for (int o = 16; o; o >>= 1) c = min(c, __shfl_xor_sync(0xffffffffu, c, o));
                 int stop = (c >= t - kSlack) || abort_flag;
                 stop = __shfl_sync(0xffffffffu, stop, 0);
@@ -125,49 +140,78 @@ sweep_one_block(int64_t N, const int64_t *__restrict__ rp, const int32_t *__rest
                 }
             }
         }
-        const int64_t b = rp[r], e = rp[r + 1];
         CT acc = O::zero();
-        for (int64_t k = b + lane; k < e; k += 32) {
-            const int32_t j = __ldcs(ci + k);
-            const CT a = __ldcs(va + k);
-            const int64_t tj = LOWER ? (int64_t)j : N - 1 - j;
-            int spins = 0;
-            uint64_t since = 0;
-            while (progress[tj & (kWarps - 1)] < tj) {
-                if (abort_flag) break;
-                if (++spins == 1024) {
-                    spins = 0;
-                    const uint64_t now = global_ns();
-                    if (!since) since = now;
-                    if (now - since > (uint64_t)timeout_ns) {
-                        abort_flag = 1;
-                        atomicExch(status, 1);
-                        break;
-                    }
+        for (int64_t base = b; base < e; base += 32 * kRegs) {
+            int32_t jj[kRegs];
+            CT aa[kRegs];
+#pragma unroll
+            for (int q = 0; q < kRegs; ++q) {
+                const int64_t k = base + q * 32 + lane;
+                if (k < e) {
+                    jj[q] = __ldcs(ci + k);
+                    aa[q] = __ldcs(va + k);
                 }
             }
-            __threadfence_block();
-            CT xj;
-            if (t - tj < WIN - kSlack) {
-                xj = vload(win + (tj & (WIN - 1)));
-            } else {
-                xj = ldcg(z + j);
+#pragma unroll
+            for (int q = 0; q < kRegs; ++q) {
+                const int64_t k = base + q * 32 + lane;
+                if (k >= e) break;
+                const int32_t j = jj[q];
+                const int64_t tj = LOWER ? (int64_t)j : N - 1 - j;
+                int spins = 0;
+                uint64_t since = 0;
+                while (progress[tj & (kWarps - 1)] < tj) {
+                    if (abort_flag) break;
+                    if (++spins == 1024) {
+                        spins = 0;
+                        const uint64_t now = global_ns();
+                        if (!since) since = now;
+                        if (now - since > (uint64_t)timeout_ns) {
+                            abort_flag = 1;
+                            atomicExch(status, 1);
+                            break;
+                        }
+                    }
+                }
+                CT xj;
+                if (t - tj < WIN - kSlack) {
+                    xj = vload(win + (tj & (WIN - 1)));
+                } else {
+                    // old value: wait until its owner has fenced it, then read L2
+                    while (committed[tj & (kWarps - 1)] < tj) {
+                        if (abort_flag) break;
+                        if (++spins == 1024) {
+                            spins = 0;
+                            const uint64_t now = global_ns();
+                            if (!since) since = now;
+                            if (now - since > (uint64_t)timeout_ns) {
+                                abort_flag = 1;
+                                atomicExch(status, 1);
+                                break;
+                            }
+                        }
+                    }
+                    xj = ldcg(z + j);
+                }
+                acc = O::fma(aa[q], xj, acc);
             }
-            acc = O::fma(a, xj, acc);
         }
         for (int o = 16; o; o >>= 1) {
             acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
             acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
         }
         if (lane == 0) {
-            CT x = O::sub(ldcg(v + r), acc);
-            if (dinv) x = O::mul(x, dinv[r]);
+            CT x = O::sub(vr, acc);
+            if (dinv) x = O::mul(x, dr);
             if (abort_flag) x = O::nan();
             vstore(win + (t & (WIN - 1)), x);
-            z[r] = x;
-            __threadfence_block();
             progress[warp] = t;
             current[warp] = t + kWarps;
+            z[r] = x;
+            if (((t / kWarps) & 31) == 31 || t + kWarps >= N) {
+                __threadfence();
+                committed[warp] = t;
+            }
         }
         __syncwarp();
     }
@@ -191,7 +235,54 @@ void launch_sweep(const om_tri &T, const CT *val, bool lower, const CT *dinv, co
     OM_CHECK_LAUNCH();
 }
 
+__global__ void narrow(const double2 *__restrict__ v, int64_t N, float2 *__restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride)
+        out[i] = make_float2((float)v[i].x, (float)v[i].y);
+}
+__global__ void widen(const float2 *__restrict__ v, int64_t N, double2 *__restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride)
+        out[i] = make_double2((double)v[i].x, (double)v[i].y);
+}
+
 }  // namespace
+
+void to_c64(const double2 *v, int64_t N, float2 *out, cudaStream_t s) {
+    int64_t need = (N + 255) / 256;
+    unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 4));
+    narrow<<<blocks, 256, 0, s>>>(v, N, out);
+    OM_CHECK_LAUNCH();
+}
+void to_c128(const float2 *v, int64_t N, double2 *out, cudaStream_t s) {
+    int64_t need = (N + 255) / 256;
+    unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 4));
+    widen<<<blocks, 256, 0, s>>>(v, N, out);
+    OM_CHECK_LAUNCH();
+}
+
+void precond_apply(const om_ilu &M, bool conj_transpose, bool fp64, const double2 *v, double2 *z, float2 *tmp32,
+                   int64_t timeout_ns, cudaStream_t s) {
+    if (fp64) {
+        if (!conj_transpose) {
+            sweep_c128(M.L, true, nullptr, v, z, M.status.p, timeout_ns, s);
+            sweep_c128(M.U, false, M.dinv.p, z, z, M.status.p, timeout_ns, s);
+        } else {
+            sweep_c128(M.UH, true, M.dinvh.p, v, z, M.status.p, timeout_ns, s);
+            sweep_c128(M.LH, false, nullptr, z, z, M.status.p, timeout_ns, s);
+        }
+        return;
+    }
+    to_c64(v, M.N, tmp32, s);
+    if (!conj_transpose) {
+        sweep_c64(M.L, true, nullptr, tmp32, tmp32, M.status.p, timeout_ns, s);
+        sweep_c64(M.U, false, M.dinv32.p, tmp32, tmp32, M.status.p, timeout_ns, s);
+    } else {
+        sweep_c64(M.UH, true, M.dinvh32.p, tmp32, tmp32, M.status.p, timeout_ns, s);
+        sweep_c64(M.LH, false, nullptr, tmp32, tmp32, M.status.p, timeout_ns, s);
+    }
+    to_c128(tmp32, M.N, z, s);
+}
 
 void sweep_c128(const om_tri &T, bool lower, const double2 *dinv, const double2 *v, double2 *z, int *status,
                 int64_t timeout_ns, cudaStream_t s) {

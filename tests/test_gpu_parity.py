@@ -1,10 +1,12 @@
 """Parity of the CUDA path (through the C ABI) with the oracle.
 
 Tolerances: integer and index data (row pointers, columns, the RCM
-permutation) bit-exact; assembled values within a few ulps (the closed-form
-stencil and the Kronecker sums round differently); vectors within 1e-12
-relative; rho within 1e-9 absolute at eta <= 1e-10 (the target the method is
-held to)."""
+permutation) bit-exact; assembled values within 16 eps ||L||_inf (the oracle
+sums up to eight Kronecker terms per entry, each rounded at the size of its
+own terms -- |H_ii| can be far larger than the difference H_ii - H_jj it
+feeds -- while the stencil forms each entry directly); vectors within
+1e-13 / 1e-10 relative to their maximum; rho within 1e-9 absolute at
+eta <= 1e-10 (the target the method is held to)."""
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -25,6 +27,10 @@ def oparams(p: SystemParams) -> Params:
     return Params(p.Nc, p.Nm, p.omega_m, p.Delta, p.kappa, p.g0, p.E, p.Q_m, p.n_th)
 
 
+def assembly_atol(L):
+    return 16 * np.finfo(float).eps * max(float(np.abs(L).sum(axis=1).max()), 1e-300)
+
+
 def gpu_csr(M):
     rp, ci, va = M.export()
     return sp.csr_matrix((va, ci, rp), shape=(M.N, M.N))
@@ -40,8 +46,7 @@ def test_assembly_matches_oracle(Nc, Nm, mode):
     rp, ci, va = A.export()
     np.testing.assert_array_equal(rp, Lt.indptr)
     np.testing.assert_array_equal(ci, Lt.indices)
-    scale = np.repeat(np.maximum(np.abs(Lt).max(axis=1).toarray().ravel(), 1e-300), np.diff(Lt.indptr))
-    assert np.all(np.abs(va - Lt.data) <= 8e-16 * scale + 1e-300)
+    assert np.abs(va - Lt.data).max(initial=0.0) <= assembly_atol(L)
     assert A.w == pytest.approx(w, rel=1e-13)
     Linf = np.abs(L).sum(axis=1).max()
     assert A.norm_inf == pytest.approx(Linf, rel=1e-14)
@@ -52,11 +57,11 @@ def test_assembly_zero_temperature_and_parameters_zero():
         p = SystemParams(3, 6, **{**BASE, **kw})
         for floor in (0.0, 1e-15):
             A = api.build_liouvillian(p, "replace", floor)
-            Lt, *_ = augmented(oparams(p), "replace", floor)
+            Lt, _, _, L = augmented(oparams(p), "replace", floor)
             rp, ci, va = A.export()
             np.testing.assert_array_equal(rp, Lt.indptr)
             np.testing.assert_array_equal(ci, Lt.indices)
-            np.testing.assert_allclose(va, Lt.data, rtol=4e-15, atol=0)
+            assert np.abs(va - Lt.data).max(initial=0.0) <= assembly_atol(L)
 
 
 def test_fig1_nnz_on_gpu():
@@ -71,14 +76,14 @@ def test_permutation_bit_exact(Nc, Nm, mode):
     p = SystemParams(Nc, Nm, **BASE)
     A = api.build_liouvillian(p, mode)
     Ar, perm = api.permute(A)
-    Lt, *_ = augmented(oparams(p), mode, 1e-15)
+    Lt, _, _, L = augmented(oparams(p), mode, 1e-15)
     ref = rcm_permutation(Lt)
     np.testing.assert_array_equal(perm.cpu().numpy(), ref)
     B = permute_symmetric(Lt, ref)
     rp, ci, va = Ar.export()
     np.testing.assert_array_equal(rp, B.indptr)
     np.testing.assert_array_equal(ci, B.indices)
-    np.testing.assert_allclose(va, B.data, rtol=4e-15, atol=0)
+    assert np.abs(va - B.data).max(initial=0.0) <= assembly_atol(L)
 
 
 # ------------------------------------------------------------------ SpMV
@@ -109,9 +114,12 @@ def test_ilu_apply_matches_oracle(Nc, Nm, d, fill):
     v = rng.standard_normal(Ar.N) + 1j * rng.standard_normal(Ar.N)
     vt = torch.from_numpy(v).cuda()
     for h in (False, True):
-        z = api.ilu_apply(M, vt, conj_transpose=h).cpu().numpy()
         ref = F.solve_h(v) if h else F.solve(v)
+        z = api.ilu_apply(M, vt, conj_transpose=h, fp64=True).cpu().numpy()
         np.testing.assert_allclose(z, ref, rtol=0, atol=1e-10 * np.abs(ref).max())
+        # complex64 sweeps: FP32 rounding amplified by the factors' conditioning
+        z32 = api.ilu_apply(M, vt, conj_transpose=h, fp64=False).cpu().numpy()
+        assert np.abs(z32 - ref).max() <= 1e-3 * np.abs(ref).max()
 
 
 def test_complete_lu_solves_exactly():
@@ -122,7 +130,7 @@ def test_complete_lu_solves_exactly():
     M = api.ilu_factor(Ar, 0.0, 1e6)
     rng = np.random.default_rng(3)
     x = torch.from_numpy(rng.standard_normal(Ar.N) + 1j * rng.standard_normal(Ar.N)).cuda()
-    z = api.ilu_apply(M, api.spmv(Ar, x))
+    z = api.ilu_apply(M, api.spmv(Ar, x), fp64=True)
     assert float((z - x).abs().max()) < 1e-9
 
 
@@ -136,9 +144,14 @@ def gpu_solve(w_params, droptol, fill, restart, tol, mode="replace", floor=1e-15
 
 
 @pytest.mark.parametrize("mode", ["replace", "add"])
-def test_tiny_solve_matches_dense_lu(mode):
+@pytest.mark.parametrize("precond_fp64", [False, True])
+def test_tiny_solve_matches_dense_lu(mode, precond_fp64):
     w = TINY
-    rho, info = gpu_solve(w.params, w.droptol, w.fill, w.restart, w.tol, mode)
+    A = api.build_liouvillian(w.params, mode)
+    Ar, perm = api.permute(A)
+    M = api.ilu_factor(Ar, w.droptol, w.fill)
+    rho, info = api.steady_state_solve(Ar, M, perm, restart=w.restart, tol=w.tol, precond_fp64=precond_fp64)
+    rho = rho.cpu().numpy()
     ref = steady_state_dense(oparams(w.params), mode).rho
     assert info.eta <= w.tol
     assert np.abs(rho - ref).max() <= 1e-9
@@ -176,11 +189,11 @@ def test_properties_at_larger_size():
     """10 x 20 (40,000 rows): eta by the oracle's own assembly, trace,
     Hermiticity and the exact cavity invariant kappa <n_a> = -2 E Im<a>."""
     p = SystemParams(10, 20, 1.0, -1.0, 0.3, 0.5, 0.3, 1e4, 1.0)
-    rho, info = gpu_solve(p, 1e-5, 100.0, 50, 1e-10)
+    rho, info = gpu_solve(p, 1e-5, 100.0, 50, 1e-11)
     n = p.n
     x = rho.reshape(-1, order="F")
     L = liouvillian(oparams(p), 1e-15)
-    assert oracle_eta(L, x) <= 1e-10
+    assert oracle_eta(L, x) <= 1e-11
     assert abs(np.trace(rho) - 1) < 1e-12
     assert np.abs(rho - rho.conj().T).max() < 1e-9
     c = np.repeat(np.arange(p.Nc), p.Nm)
