@@ -132,7 +132,10 @@ om_status om_permute(const om_matrix *A, void *stream, int32_t *perm_dev, om_mat
  * the smaller column), so NNZ(L) + NNZ(U) <= fill * NNZ(A).  A pivot below
  * 1e-14 ||row i||_inf is replaced by that value and counted.
  * flags bit 0: add the moduli of the entries dropped from row i to |u_ii|
- * (diagonal compensation).  Errors: OM_EINVAL, OM_ENOMEM. */
+ * (diagonal compensation); bit 1: also store the conjugate transposes U^H,
+ * L^H needed by the adjoint.  Rows are factored in parallel on the host
+ * cores (OMSS_ILU_THREADS caps the thread count); the factors are identical
+ * to those of the serial row order.  Errors: OM_EINVAL, OM_ENOMEM. */
 om_status om_ilu_factor(const om_matrix *A_rcm, double droptol, double fill, int32_t flags,
                         void *stream, om_ilu **out);
 
@@ -177,6 +180,17 @@ om_status om_ilu_apply(const om_ilu *M, int32_t flags, const double *v, double *
 /* <a^dag a>, <b^dag b> of a DEVICE rho (c128 n x n column-major); out HOST double[2]. */
 om_status om_observables(int32_t Nc, int32_t Nm, const double *rho_dev, double out[2],
                          void *stream);
+
+/* ---- instrumentation (no counterpart in the paper) -------------------------
+ * om_kernel_launches: number of kernels the library has launched since it was
+ * loaded.  om_profile(1) starts recording CUDA events around every triangular
+ * sweep (category 0) and SpMV (category 1) launch, om_profile(0) stops, both
+ * discard earlier records; om_profile_read returns the summed device time
+ * (milliseconds, HOST out) and launch count of a category, synchronising on
+ * the recorded events. */
+int64_t om_kernel_launches(void);
+om_status om_profile(int32_t enable);
+om_status om_profile_read(int32_t category, double *total_ms, int64_t *count);
 
 void om_matrix_free(om_matrix *A);
 void om_ilu_free(om_ilu *M);

@@ -50,6 +50,9 @@ SIGNATURES = {
     "om_spmv": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
     "om_ilu_apply": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp]),
     "om_observables": (c_i32, [c_i32, c_i32, c_vp, ctypes.POINTER(c_dbl * 2), c_vp]),
+    "om_kernel_launches": (c_i64, []),
+    "om_profile": (c_i32, [c_i32]),
+    "om_profile_read": (c_i32, [c_i32, ctypes.POINTER(c_dbl), ctypes.POINTER(c_i64)]),
     "om_matrix_free": (None, [c_vp]),
     "om_ilu_free": (None, [c_vp]),
     "om_status_str": (ctypes.c_char_p, [c_i32]),

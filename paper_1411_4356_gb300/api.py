@@ -122,11 +122,13 @@ def permute(A: Matrix, stream=None):
     return Matrix(out.value, A.params), perm
 
 
-def ilu_factor(A: Matrix, droptol: float, fill: float, compensate: bool = False, stream=None) -> ILU:
-    """Sec. II: ILUT(droptol, fill) of a permuted matrix."""
+def ilu_factor(A: Matrix, droptol: float, fill: float, compensate: bool = False, adjoint: bool = False,
+               stream=None) -> ILU:
+    """Sec. II: ILUT(droptol, fill) of a permuted matrix; adjoint=True also keeps
+    the conjugate-transposed factors for the adjoint sweeps."""
     lib = _lib.load()
     out = ctypes.c_void_p()
-    check(lib.om_ilu_factor(A.handle, float(droptol), float(fill), 1 if compensate else 0,
+    check(lib.om_ilu_factor(A.handle, float(droptol), float(fill), (1 if compensate else 0) | (2 if adjoint else 0),
                             ctypes.c_void_p(_stream(stream)), ctypes.byref(out)), "om_ilu_factor")
     return ILU(out.value, A.nnz)
 
@@ -215,3 +217,23 @@ def observables(Nc: int, Nm: int, rho: torch.Tensor, stream=None):
     check(_lib.load().om_observables(int(Nc), int(Nm), _ptr(flat), ctypes.byref(out),
                                      ctypes.c_void_p(_stream(stream))), "om_observables")
     return out[0], out[1]
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libomss.so since it was loaded."""
+    return int(_lib.load().om_kernel_launches())
+
+
+PROF_SWEEP, PROF_SPMV = 0, 1
+
+
+def profile(enable: bool) -> None:
+    """Start (True) or stop (False) event timing of sweep and SpMV launches."""
+    check(_lib.load().om_profile(1 if enable else 0), "om_profile")
+
+
+def profile_read(category: int):
+    """(total device milliseconds, launch count) recorded for a category."""
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    check(_lib.load().om_profile_read(int(category), ctypes.byref(ms), ctypes.byref(n)), "om_profile_read")
+    return ms.value, n.value

@@ -1,14 +1,40 @@
 // Status strings, per-thread error messages and small handle queries.
+#include <atomic>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <tuple>
 
 #include "common.cuh"
 
 namespace omss {
 namespace {
 thread_local std::string g_last_error;
-}
+std::atomic<int64_t> g_launches{0};
+struct ProfState {
+    std::atomic<bool> on{false};
+    std::mutex mu;
+    std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> events;
+};
+ProfState g_prof;
+}  // namespace
 void set_error(const std::string &msg) { g_last_error = msg; }
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+ProfScope::ProfScope(int cat_, cudaStream_t s_) : cat(cat_), s(s_), on(g_prof.on.load()) {
+    if (on) {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, s);
+    }
+}
+ProfScope::~ProfScope() {
+    if (on) {
+        cudaEventRecord(b, s);
+        std::lock_guard<std::mutex> g(g_prof.mu);
+        g_prof.events.emplace_back(cat, a, b);
+    }
+}
 }  // namespace omss
 
 using namespace omss;
@@ -29,6 +55,40 @@ extern "C" const char *om_status_str(om_status s) {
 }
 
 extern "C" const char *om_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int64_t om_kernel_launches(void) { return g_launches.load(); }
+
+extern "C" om_status om_profile(int32_t enable) {
+    return guarded([&] {
+        std::lock_guard<std::mutex> g(g_prof.mu);
+        for (auto &e : g_prof.events) {
+            cudaEventSynchronize(std::get<2>(e));
+            cudaEventDestroy(std::get<1>(e));
+            cudaEventDestroy(std::get<2>(e));
+        }
+        g_prof.events.clear();
+        g_prof.on = enable != 0;
+    });
+}
+
+extern "C" om_status om_profile_read(int32_t category, double *total_ms, int64_t *count) {
+    return guarded([&] {
+        OM_REQUIRE(category >= 0 && category < PROF_CATEGORIES, "om_profile_read: bad category");
+        std::lock_guard<std::mutex> g(g_prof.mu);
+        double ms = 0;
+        int64_t n = 0;
+        for (auto &e : g_prof.events) {
+            if (std::get<0>(e) != category) continue;
+            OM_CUDA_TRY(cudaEventSynchronize(std::get<2>(e)));
+            float t = 0;
+            OM_CUDA_TRY(cudaEventElapsedTime(&t, std::get<1>(e), std::get<2>(e)));
+            ms += t;
+            ++n;
+        }
+        if (total_ms) *total_ms = ms;
+        if (count) *count = n;
+    });
+}
 
 extern "C" om_status om_matrix_info(const om_matrix *A, int64_t *nrows, int64_t *nnz, double *w,
                                     double *norm_inf) {

@@ -224,7 +224,7 @@ extern "C" om_status om_build_liouvillian(const om_params *params, const om_buil
         OM_CUDA_TRY(cudaMemsetAsync(normbits.p, 0, sizeof(double), s));
         const int T = 256;
         const unsigned blocks = (unsigned)((N + T - 1) / T);
-        count_rows<<<blocks, T, 0, s>>>(M, N, counts.p, normbits.p);
+        count_rows<<<blocks, T, 0, s>>>(M, N, counts.p, normbits.p); omss::note_launch();
         OM_CHECK_LAUNCH();
         int64_t c0count = (int64_t)tcol.size();
         OM_CUDA_TRY(cudaMemcpyAsync(counts.p, &c0count, sizeof(int64_t), cudaMemcpyHostToDevice, s));
@@ -240,7 +240,7 @@ extern "C" om_status om_build_liouvillian(const om_params *params, const om_buil
         A->norm_inf = norm;
         A->col.alloc(nnz, s);
         A->val.alloc(nnz, s);
-        fill_rows<<<blocks, T, 0, s>>>(M, N, A->rowptr.p, A->col.p, A->val.p);
+        fill_rows<<<blocks, T, 0, s>>>(M, N, A->rowptr.p, A->col.p, A->val.p); omss::note_launch();
         OM_CHECK_LAUNCH();
         OM_CUDA_TRY(cudaMemcpyAsync(A->col.p, tcol.data(), sizeof(int32_t) * tcol.size(),
                                     cudaMemcpyHostToDevice, s));
@@ -255,7 +255,7 @@ extern "C" om_status om_build_liouvillian(const om_params *params, const om_buil
         OM_CUDA_TRY(cudaMemcpyAsync(A->d_row0_val.p, A->row0_val.data(), sizeof(double2) * cnt0,
                                     cudaMemcpyHostToDevice, s));
         A->diag_pos.alloc(n, s);
-        diag_positions<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((int32_t)n, A->diag_pos.p);
+        diag_positions<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((int32_t)n, A->diag_pos.p); omss::note_launch();
         OM_CHECK_LAUNCH();
         counts.release(s);
         scratch.release(s);

@@ -15,6 +15,21 @@ namespace omss {
 
 void set_error(const std::string &msg);
 
+// Counts every kernel launch of the library (om_kernel_launches).
+void note_launch();
+
+// Kernel timing by CUDA events, active between om_profile(1) and om_profile(0).
+// Categories: 0 = triangular sweeps, 1 = SpMV.
+enum { PROF_SWEEP = 0, PROF_SPMV = 1, PROF_CATEGORIES = 2 };
+struct ProfScope {
+    int cat;
+    cudaStream_t s;
+    bool on;
+    cudaEvent_t a{}, b{};
+    ProfScope(int cat_, cudaStream_t s_);
+    ~ProfScope();
+};
+
 struct Error {
     om_status status;
     std::string msg;
@@ -163,6 +178,7 @@ struct om_ilu {
     om_tri UH;
     om_tri LH;
     int64_t n_guarded = 0;
+    bool has_transpose = false;
     omss::DBuf<int> status;     // device status word for bounded waits
     cudaStream_t owner_stream = nullptr;
     ~om_ilu();

@@ -11,8 +11,9 @@
 // pivoting (after the reordering the diagonal of L~ is zero-free); a pivot
 // below 1e-14 ||row i||_inf is replaced by that value and counted.
 //
-// The factorisation runs on the host (it is the serial setup stage of the
-// method); the factors are then laid out on the device for the sweeps:
+// The factorisation runs on the host cores (it is the setup stage of the
+// method; the paper runs it serially), row-parallel over all cores; the
+// factors are then laid out on the device for the sweeps:
 // strict L, strict U and 1/u_ii in CSR (int64 row pointers, int32 columns,
 // c128 values), plus complex64 copies and the conjugate transposes U^H, L^H
 // used by the adjoint.
@@ -21,6 +22,9 @@
 #include <complex>
 #include <memory>
 #include <queue>
+#include <atomic>
+#include <cstdlib>
+#include <thread>
 
 #include "common.cuh"
 
@@ -40,25 +44,49 @@ struct Picked {
     double mag;
 };
 
-void ilut_host(int64_t N, const std::vector<int64_t> &arp, const std::vector<int32_t> &aci,
-               const std::vector<double2> &ava, double droptol, double fill, bool compensate,
-               HostTri &L, HostTri &U, std::vector<cd> &diag, int64_t &guarded) {
+// Row-parallel ILUT on the host.  Rows are claimed in increasing order from
+// an atomic counter; a row eliminates with U rows of earlier rows as soon as
+// their owners publish them (release/acquire flags), so only eliminations
+// with recent rows wait.  Each row writes into preallocated slots sized by
+// the fill cap, compacted afterwards; the result is bitwise the same as the
+// serial elimination order.
+struct IlutShared {
+    int64_t N;
+    const std::vector<int64_t> *arp;
+    const std::vector<int32_t> *aci;
+    const std::vector<double2> *ava;
+    double droptol, fill;
+    bool compensate;
+    std::vector<int64_t> slot;   // per-row slot offset (cap_i entries each for L and U)
+    std::vector<int32_t> lcnt, ucnt;
+    std::vector<int32_t> lci, uci;
+    std::vector<cd> lva, uva;
+    std::vector<cd> diag;
+    std::unique_ptr<std::atomic<int>[]> done;
+    std::atomic<int64_t> next{0};
+    std::atomic<int64_t> guarded{0};
+};
+
+void ilut_worker(IlutShared &S) {
+    const int64_t N = S.N;
+    const auto &arp = *S.arp;
+    const auto &aci = *S.aci;
+    const auto &ava = *S.ava;
     std::vector<cd> w(N, cd(0, 0));
     std::vector<char> in_row(N, 0);
     std::vector<int32_t> present;
     std::vector<Picked> lo, hi;
     std::priority_queue<int32_t, std::vector<int32_t>, std::greater<int32_t>> pending;
-    L.rp.assign(N + 1, 0);
-    U.rp.assign(N + 1, 0);
-    diag.assign(N, cd(0, 0));
-    guarded = 0;
     auto by_size = [](const Picked &a, const Picked &b) { return a.mag != b.mag ? a.mag > b.mag : a.c < b.c; };
-    for (int64_t i = 0; i < N; ++i) {
+    auto by_col = [](const Picked &a, const Picked &b) { return a.c < b.c; };
+    for (;;) {
+        const int64_t i = S.next.fetch_add(1, std::memory_order_relaxed);
+        if (i >= N) break;
         const int64_t nnz_i = arp[i + 1] - arp[i];
         double anorm = 0;
         for (int64_t e = arp[i]; e < arp[i + 1]; ++e) anorm = std::max(anorm, std::abs(cd(ava[e].x, ava[e].y)));
-        const double tau = droptol * anorm;
-        int64_t cap = (int64_t)std::floor(fill * (double)nnz_i / 2.0);
+        const double tau = S.droptol * anorm;
+        int64_t cap = (int64_t)std::floor(S.fill * (double)nnz_i / 2.0);
         if (cap < 1) cap = 1;
         present.clear();
         for (int64_t e = arp[i]; e < arp[i + 1]; ++e) {
@@ -77,22 +105,25 @@ void ilut_host(int64_t N, const std::vector<int64_t> &arp, const std::vector<int
         while (!pending.empty()) {
             int32_t k = pending.top();
             pending.pop();
-            cd m = w[k] / diag[k];
+            for (int spins = 0; !S.done[k].load(std::memory_order_acquire); ++spins)
+                if (spins > 64) std::this_thread::yield();
+            cd m = w[k] / S.diag[k];
             if (std::abs(m) < tau) {
                 dropped += std::abs(w[k]);
                 w[k] = 0;
                 continue;
             }
             w[k] = m;
-            for (int64_t e = U.rp[k]; e < U.rp[k + 1]; ++e) {
-                int32_t c = U.ci[e];
+            const int64_t ub = S.slot[k], ue = ub + S.ucnt[k];
+            for (int64_t e = ub; e < ue; ++e) {
+                int32_t c = S.uci[e];
                 if (!in_row[c]) {
                     in_row[c] = 1;
                     w[c] = 0;
                     present.push_back(c);
                     if (c < i) pending.push(c);
                 }
-                w[c] -= m * U.va[e];
+                w[c] -= m * S.uva[e];
             }
         }
         lo.clear();
@@ -110,7 +141,7 @@ void ilut_host(int64_t N, const std::vector<int64_t> &arp, const std::vector<int
         }
         if ((int64_t)lo.size() > cap) {
             std::nth_element(lo.begin(), lo.begin() + cap, lo.end(), by_size);
-            for (size_t t = cap; t < lo.size(); ++t) dropped += lo[t].mag * std::abs(diag[lo[t].c]);
+            for (size_t t = cap; t < lo.size(); ++t) dropped += lo[t].mag * std::abs(S.diag[lo[t].c]);
             lo.resize(cap);
         }
         if ((int64_t)hi.size() > cap - 1) {
@@ -118,32 +149,88 @@ void ilut_host(int64_t N, const std::vector<int64_t> &arp, const std::vector<int
             for (size_t t = cap - 1; t < hi.size(); ++t) dropped += hi[t].mag;
             hi.resize(cap - 1);
         }
-        auto by_col = [](const Picked &a, const Picked &b) { return a.c < b.c; };
         std::sort(lo.begin(), lo.end(), by_col);
         std::sort(hi.begin(), hi.end(), by_col);
-        for (auto &t : lo) {
-            L.ci.push_back(t.c);
-            L.va.push_back(w[t.c]);
+        const int64_t base = S.slot[i];
+        for (size_t t = 0; t < lo.size(); ++t) {
+            S.lci[base + t] = lo[t].c;
+            S.lva[base + t] = w[lo[t].c];
         }
-        L.rp[i + 1] = (int64_t)L.ci.size();
+        S.lcnt[i] = (int32_t)lo.size();
         cd piv = w[i];
-        if (compensate && dropped > 0) piv = (std::abs(piv) > 0) ? piv + dropped * piv / std::abs(piv) : cd(dropped, 0);
+        if (S.compensate && dropped > 0)
+            piv = (std::abs(piv) > 0) ? piv + dropped * piv / std::abs(piv) : cd(dropped, 0);
         const double floor_ = 1e-14 * anorm;
         if (std::abs(piv) < floor_ || piv == cd(0, 0)) {
             piv = cd(floor_ > 0 ? floor_ : 1e-300, 0);
-            ++guarded;
+            S.guarded.fetch_add(1, std::memory_order_relaxed);
         }
-        diag[i] = piv;
-        for (auto &t : hi) {
-            U.ci.push_back(t.c);
-            U.va.push_back(w[t.c]);
+        S.diag[i] = piv;
+        for (size_t t = 0; t < hi.size(); ++t) {
+            S.uci[base + t] = hi[t].c;
+            S.uva[base + t] = w[hi[t].c];
         }
-        U.rp[i + 1] = (int64_t)U.ci.size();
+        S.ucnt[i] = (int32_t)hi.size();
+        S.done[i].store(1, std::memory_order_release);
         for (int32_t c : present) {
             w[c] = 0;
             in_row[c] = 0;
         }
     }
+}
+
+void ilut_host(int64_t N, const std::vector<int64_t> &arp, const std::vector<int32_t> &aci,
+               const std::vector<double2> &ava, double droptol, double fill, bool compensate,
+               HostTri &L, HostTri &U, std::vector<cd> &diag, int64_t &guarded) {
+    IlutShared S;
+    S.N = N;
+    S.arp = &arp;
+    S.aci = &aci;
+    S.ava = &ava;
+    S.droptol = droptol;
+    S.fill = fill;
+    S.compensate = compensate;
+    S.slot.assign(N + 1, 0);
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t cap = (int64_t)std::floor(fill * (double)(arp[i + 1] - arp[i]) / 2.0);
+        S.slot[i + 1] = S.slot[i] + std::max<int64_t>(cap, 1);
+    }
+    const int64_t total = S.slot[N];
+    S.lcnt.assign(N, 0);
+    S.ucnt.assign(N, 0);
+    S.lci.resize(total);
+    S.uci.resize(total);
+    S.lva.resize(total);
+    S.uva.resize(total);
+    S.diag.assign(N, cd(0, 0));
+    S.done.reset(new std::atomic<int>[N > 0 ? N : 1]);
+    for (int64_t i = 0; i < N; ++i) S.done[i].store(0, std::memory_order_relaxed);
+    unsigned nt = std::max(1u, std::thread::hardware_concurrency());
+    if (const char *env = std::getenv("OMSS_ILU_THREADS")) nt = std::max(1, std::atoi(env));
+    if ((int64_t)nt > N) nt = (unsigned)std::max<int64_t>(1, N);
+    std::vector<std::thread> pool;
+    for (unsigned t = 1; t < nt; ++t) pool.emplace_back(ilut_worker, std::ref(S));
+    ilut_worker(S);
+    for (auto &th : pool) th.join();
+    // compact the slots into CSR
+    L.rp.assign(N + 1, 0);
+    U.rp.assign(N + 1, 0);
+    for (int64_t i = 0; i < N; ++i) {
+        L.rp[i + 1] = L.rp[i] + S.lcnt[i];
+        U.rp[i + 1] = U.rp[i] + S.ucnt[i];
+    }
+    L.ci.resize(L.rp[N]);
+    L.va.resize(L.rp[N]);
+    U.ci.resize(U.rp[N]);
+    U.va.resize(U.rp[N]);
+    for (int64_t i = 0; i < N; ++i) {
+        std::copy(S.lci.begin() + S.slot[i], S.lci.begin() + S.slot[i] + S.lcnt[i], L.ci.begin() + L.rp[i]);
+        std::copy(S.lva.begin() + S.slot[i], S.lva.begin() + S.slot[i] + S.lcnt[i], L.va.begin() + L.rp[i]);
+        std::copy(S.uci.begin() + S.slot[i], S.uci.begin() + S.slot[i] + S.ucnt[i], U.ci.begin() + U.rp[i]);
+        std::copy(S.uva.begin() + S.slot[i], S.uva.begin() + S.slot[i] + S.ucnt[i], U.va.begin() + U.rp[i]);
+    }
+    diag.swap(S.diag);
+    guarded = S.guarded.load();
 }
 
 // Conjugate transpose of a strict triangular CSR.
@@ -242,11 +329,16 @@ extern "C" om_status om_ilu_factor(const om_matrix *A, double droptol, double fi
         upload(M->U, N, U, true, s);
         M->L.levels = dag_depth(N, L, true);
         M->U.levels = dag_depth(N, U, false);
-        HostTri UH = conj_transpose(N, U), LH = conj_transpose(N, L);
-        upload(M->UH, N, UH, true, s);
-        upload(M->LH, N, LH, true, s);
-        M->UH.levels = M->U.levels;
-        M->LH.levels = M->L.levels;
+        HostTri UH, LH;
+        if (flags & 2) {  // conjugate transposes for the adjoint sweeps
+            UH = conj_transpose(N, U);
+            LH = conj_transpose(N, L);
+            upload(M->UH, N, UH, true, s);
+            upload(M->LH, N, LH, true, s);
+            M->UH.levels = M->U.levels;
+            M->LH.levels = M->L.levels;
+            M->has_transpose = true;
+        }
         std::vector<double2> dinv(N);
         std::vector<double2> dinvh(N);
         std::vector<float2> dinv32(N), dinvh32(N);

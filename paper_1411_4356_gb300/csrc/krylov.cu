@@ -286,7 +286,7 @@ static unsigned grid_for(int64_t N) {
 }
 
 void dev_axpby(double2 a, const double2 *x, double2 b, double2 *y, int64_t N, cudaStream_t s) {
-    axpby_kernel<<<grid_for(N), kThreads, 0, s>>>(a, x, b, y, N);
+    axpby_kernel<<<grid_for(N), kThreads, 0, s>>>(a, x, b, y, N); omss::note_launch();
     OM_CHECK_LAUNCH();
 }
 void dev_copy(const double2 *x, double2 *y, int64_t N, cudaStream_t s) {
@@ -300,8 +300,8 @@ void dev_zero(double2 *x, int64_t N, cudaStream_t s) {
 static void stats(const double2 *x, int64_t N, GmresWork &W, cudaStream_t s, double *out2) {
     int nb = reduce_blocks(N);
     double *ps = W.scal.p + 8, *pm = W.scal.p + 8 + 2048;
-    vec_stats<<<nb, kThreads, 0, s>>>(x, N, ps, pm);
-    finish_stats<<<1, 32, 0, s>>>(ps, pm, nb, W.scal.p + 2);
+    vec_stats<<<nb, kThreads, 0, s>>>(x, N, ps, pm); omss::note_launch();
+    finish_stats<<<1, 32, 0, s>>>(ps, pm, nb, W.scal.p + 2); omss::note_launch();
     OM_CHECK_LAUNCH();
     OM_CUDA_TRY(cudaMemcpyAsync(out2, W.scal.p + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     OM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -337,8 +337,8 @@ GmresResult gmres_cycle(KrylovOps &ops, const double2 *b, double2 *x, double tar
         return res;
     }
     OM_CUDA_TRY(cudaMemcpyAsync(d_nrm, W.scal.p + 2, sizeof(double), cudaMemcpyDeviceToDevice, s));
-    scale_into<<<grid_for(N), kThreads, 0, s>>>(W.r.p, d_nrm, N, W.V.p);
-    init_g<<<1, 128, 0, s>>>(W.g.p, m + 2, d_nrm);
+    scale_into<<<grid_for(N), kThreads, 0, s>>>(W.r.p, d_nrm, N, W.V.p); omss::note_launch();
+    init_g<<<1, 128, 0, s>>>(W.g.p, m + 2, d_nrm); omss::note_launch();
     OM_CHECK_LAUNCH();
     int k = 0;
     double est = beta;
@@ -352,22 +352,22 @@ GmresResult gmres_cycle(KrylovOps &ops, const double2 *b, double2 *x, double tar
         for (int pass = 0; pass < 2; ++pass) {
             for (int f = 0; f <= j; f += kChunk) {
                 int cnt = std::min(kChunk, j + 1 - f);
-                multidot<<<nb, kThreads, 0, s>>>(W.V.p, N, f, cnt, W.w.p, W.partial.p, ld);
+                multidot<<<nb, kThreads, 0, s>>>(W.V.p, N, f, cnt, W.w.p, W.partial.p, ld); omss::note_launch();
             }
-            finish_dots<<<1, 128, 0, s>>>(W.partial.p, nb, j + 1, ld, W.h.p, pass);
+            finish_dots<<<1, 128, 0, s>>>(W.partial.p, nb, j + 1, ld, W.h.p, pass); omss::note_launch();
             // second pass corrects with the re-orthogonalisation coefficients only
             if (pass == 0) {
-                multi_axpy<<<nb, kThreads, 0, s>>>(W.V.p, N, j + 1, W.h.p, W.w.p, nullptr);
+                multi_axpy<<<nb, kThreads, 0, s>>>(W.V.p, N, j + 1, W.h.p, W.w.p, nullptr); omss::note_launch();
             } else {
                 // h holds h1 + h2; the update uses h2 = partial sums just computed
-                finish_dots<<<1, 128, 0, s>>>(W.partial.p, nb, j + 1, ld, W.y.p, 0);
-                multi_axpy<<<nb, kThreads, 0, s>>>(W.V.p, N, j + 1, W.y.p, W.w.p, W.scal.p + 8);
-                finish_norm<<<1, 32, 0, s>>>(W.scal.p + 8, nb, d_nrm);
+                finish_dots<<<1, 128, 0, s>>>(W.partial.p, nb, j + 1, ld, W.y.p, 0); omss::note_launch();
+                multi_axpy<<<nb, kThreads, 0, s>>>(W.V.p, N, j + 1, W.y.p, W.w.p, W.scal.p + 8); omss::note_launch();
+                finish_norm<<<1, 32, 0, s>>>(W.scal.p + 8, nb, d_nrm); omss::note_launch();
             }
             OM_CHECK_LAUNCH();
         }
-        scale_into<<<grid_for(N), kThreads, 0, s>>>(W.w.p, d_nrm, N, vnext);
-        givens_step<<<1, 1, 0, s>>>(W.H.p, m + 1, W.cs.p, W.sn.p, W.g.p, W.h.p, d_nrm, j, d_est);
+        scale_into<<<grid_for(N), kThreads, 0, s>>>(W.w.p, d_nrm, N, vnext); omss::note_launch();
+        givens_step<<<1, 1, 0, s>>>(W.H.p, m + 1, W.cs.p, W.sn.p, W.g.p, W.h.p, d_nrm, j, d_est); omss::note_launch();
         OM_CHECK_LAUNCH();
         double hn[2];
         OM_CUDA_TRY(cudaMemcpyAsync(hn, W.scal.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -383,8 +383,8 @@ GmresResult gmres_cycle(KrylovOps &ops, const double2 *b, double2 *x, double tar
     }
     res.last_estimate = est;
     if (k > 0) {
-        back_substitute<<<1, 1, 0, s>>>(W.H.p, m + 1, W.g.p, k, W.y.p);
-        combine<<<grid_for(N), kThreads, 0, s>>>(W.Z.p, N, k, W.y.p, W.w.p);
+        back_substitute<<<1, 1, 0, s>>>(W.H.p, m + 1, W.g.p, k, W.y.p); omss::note_launch();
+        combine<<<grid_for(N), kThreads, 0, s>>>(W.Z.p, N, k, W.y.p, W.w.p); omss::note_launch();
         OM_CHECK_LAUNCH();
         dev_axpby(make_double2(1, 0), W.w.p, make_double2(1, 0), x, N, s);
     }

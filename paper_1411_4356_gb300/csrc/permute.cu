@@ -194,18 +194,18 @@ extern "C" om_status om_permute(const om_matrix *A, void *stream, int32_t *perm_
         d_iperm.alloc(N, s);
         const int T = 256;
         const unsigned blocks = (unsigned)((N + T - 1) / T);
-        invert_perm<<<blocks, T, 0, s>>>(perm_dev, N, d_iperm.p);
+        invert_perm<<<blocks, T, 0, s>>>(perm_dev, N, d_iperm.p); omss::note_launch();
         DBuf<int64_t> counts, scratch;
         counts.alloc(N, s);
         scratch.alloc(scan_scratch_size(N), s);
-        permuted_counts<<<blocks, T, 0, s>>>(perm_dev, A->rowptr.p, N, counts.p);
+        permuted_counts<<<blocks, T, 0, s>>>(perm_dev, A->rowptr.p, N, counts.p); omss::note_launch();
         OM_CHECK_LAUNCH();
         B->rowptr.alloc(N + 1, s);
         exclusive_scan_counts(counts.p, B->rowptr.p, N, scratch.p, s);
         B->col.alloc(B->nnz, s);
         B->val.alloc(B->nnz, s);
         permute_rows<<<blocks, T, 0, s>>>(perm_dev, d_iperm.p, A->rowptr.p, A->col.p, A->val.p, N,
-                                          B->rowptr.p, B->col.p, B->val.p);
+                                          B->rowptr.p, B->col.p, B->val.p); omss::note_launch();
         OM_CHECK_LAUNCH();
         // long rows (the trace row): sort on the host
         std::vector<int64_t> prp(N + 1);

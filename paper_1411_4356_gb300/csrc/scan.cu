@@ -86,9 +86,9 @@ void exclusive_scan_counts(const int64_t *counts, int64_t *rowptr, int64_t N, in
         return;
     }
     int64_t ntiles = (N + kTile - 1) / kTile;
-    tile_sums<<<(unsigned)ntiles, kScanThreads, 0, s>>>(counts, N, scratch);
-    scan_sums<<<1, 1024, 0, s>>>(scratch, ntiles);
-    tile_scan<<<(unsigned)ntiles, kScanThreads, 0, s>>>(counts, N, scratch, rowptr);
+    tile_sums<<<(unsigned)ntiles, kScanThreads, 0, s>>>(counts, N, scratch); omss::note_launch();
+    scan_sums<<<1, 1024, 0, s>>>(scratch, ntiles); omss::note_launch();
+    tile_scan<<<(unsigned)ntiles, kScanThreads, 0, s>>>(counts, N, scratch, rowptr); omss::note_launch();
     OM_CHECK_LAUNCH();
 }
 

@@ -96,7 +96,7 @@ struct ForwardOps : KrylovOps {
 // eta of x for the unmodified Liouvillian; y is scratch of length N
 double eta_of(const om_matrix &A, const double2 *x, double2 *y, GmresWork &W, cudaStream_t s) {
     spmv_c128(A.rowptr.p, A.col.p, A.val.p, A.N, x, y, s);
-    fix_trace_row<<<1, 1, 0, s>>>(y, x, A.trace_row, A.d_row0_col.p, A.d_row0_val.p, (int)A.row0_col.size());
+    fix_trace_row<<<1, 1, 0, s>>>(y, x, A.trace_row, A.d_row0_col.p, A.d_row0_val.p, (int)A.row0_col.size()); omss::note_launch();
     OM_CHECK_LAUNCH();
     double ly = dev_maxabs(y, A.N, W, s);
     double lx = dev_maxabs(x, A.N, W, s);
@@ -105,7 +105,7 @@ double eta_of(const om_matrix &A, const double2 *x, double2 *y, GmresWork &W, cu
 
 double2 trace_of(const om_matrix &A, const double2 *x, GmresWork &W, cudaStream_t s) {
     double2 *t = reinterpret_cast<double2 *>(W.scal.p + 4);
-    gather_sum<<<1, 256, 0, s>>>(x, A.diag_pos.p, A.n, t);
+    gather_sum<<<1, 256, 0, s>>>(x, A.diag_pos.p, A.n, t); omss::note_launch();
     OM_CHECK_LAUNCH();
     double2 h;
     OM_CUDA_TRY(cudaMemcpyAsync(&h, t, sizeof(double2), cudaMemcpyDeviceToHost, s));
@@ -116,10 +116,10 @@ double2 trace_of(const om_matrix &A, const double2 *x, GmresWork &W, cudaStream_
 void normalise_into_rho(const om_matrix &A, const double2 *x, const int32_t *perm, double2 *rho, GmresWork &W,
                         cudaStream_t s) {
     double2 *t = reinterpret_cast<double2 *>(W.scal.p + 4);
-    gather_sum<<<1, 256, 0, s>>>(x, A.diag_pos.p, A.n, t);
+    gather_sum<<<1, 256, 0, s>>>(x, A.diag_pos.p, A.n, t); omss::note_launch();
     int64_t need = (A.N + 255) / 256;
     unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 4));
-    normalise_scatter<<<blocks, 256, 0, s>>>(x, perm, A.N, t, rho);
+    normalise_scatter<<<blocks, 256, 0, s>>>(x, perm, A.N, t, rho); omss::note_launch();
     OM_CHECK_LAUNCH();
 }
 
@@ -159,7 +159,7 @@ extern "C" om_status om_steady_state_solve(const om_matrix *A, const om_ilu *M, 
         b.alloc(N, s);
         x.alloc(N, s);
         dev_zero(b.p, N, s);
-        set_entry<<<1, 1, 0, s>>>(b.p, A->trace_row, make_double2(A->w, 0));
+        set_entry<<<1, 1, 0, s>>>(b.p, A->trace_row, make_double2(A->w, 0)); omss::note_launch();
         OM_CHECK_LAUNCH();
         if (x0) dev_copy(reinterpret_cast<const double2 *>(x0), x.p, N, s);
         else dev_zero(x.p, N, s);
@@ -226,6 +226,7 @@ extern "C" om_status om_ilu_apply(const om_ilu *M, int32_t flags, const double *
     const int32_t conj_transpose = flags & 2 ? 1 : 0;
     return guarded([&] {
         OM_REQUIRE(M && v && z, "om_ilu_apply: NULL argument");
+        OM_REQUIRE(!(flags & 2) || M->has_transpose, "om_ilu_apply: factor built without conjugate transposes");
         cudaStream_t s = as_stream(stream);
         const double2 *vv = reinterpret_cast<const double2 *>(v);
         double2 *zz = reinterpret_cast<double2 *>(z);
@@ -247,7 +248,7 @@ extern "C" om_status om_observables(int32_t Nc, int32_t Nm, const double *rho_de
         cudaStream_t s = as_stream(stream);
         DBuf<double> d;
         d.alloc(2, s);
-        observables_kernel<<<1, 256, 0, s>>>(Nc, Nm, reinterpret_cast<const double2 *>(rho_dev), d.p);
+        observables_kernel<<<1, 256, 0, s>>>(Nc, Nm, reinterpret_cast<const double2 *>(rho_dev), d.p); omss::note_launch();
         OM_CHECK_LAUNCH();
         OM_CUDA_TRY(cudaMemcpyAsync(out, d.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
         OM_CUDA_TRY(cudaStreamSynchronize(s));

@@ -69,7 +69,8 @@ void launch(const int64_t *rowptr, const int32_t *col, const CT *val, int64_t N,
     int64_t need = (N + (T / G) - 1) / (T / G);
     int64_t cap = (int64_t)num_sms() * 8;
     unsigned blocks = (unsigned)std::max<int64_t>(1, std::min(need, cap));
-    spmv_kernel<G, CT><<<blocks, T, 0, s>>>(rowptr, col, val, N, x, y);
+    ProfScope prof(PROF_SPMV, s);
+    spmv_kernel<G, CT><<<blocks, T, 0, s>>>(rowptr, col, val, N, x, y); omss::note_launch();
     OM_CHECK_LAUNCH();
 }
 

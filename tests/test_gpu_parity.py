@@ -106,7 +106,7 @@ def test_ilu_apply_matches_oracle(Nc, Nm, d, fill):
     p = SystemParams(Nc, Nm, **BASE)
     A = api.build_liouvillian(p)
     Ar, perm = api.permute(A)
-    M = api.ilu_factor(Ar, d, fill)
+    M = api.ilu_factor(Ar, d, fill, adjoint=True)
     B = gpu_csr(Ar)
     F = ilut(B, d, fill)
     assert M.nnz_l == F.nnz_l and M.nnz_u == F.nnz_u
