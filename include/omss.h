@@ -177,6 +177,22 @@ om_status om_spmv(const om_matrix *A, const double *x, double *y, void *stream);
  * bit 1: apply the conjugate transpose.  Errors: OM_EINVAL, OM_ETIMEOUT. */
 om_status om_ilu_apply(const om_ilu *M, int32_t flags, const double *v, double *z,
                        void *stream);
+/* Allocation-free variant of om_ilu_apply.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory --
+ * code whose device memory belongs to another allocator (a framework's
+ * caching pool), and latency-critical code that must not enter the allocator
+ * or risk the implicit device synchronisation of cudaMalloc/cudaFree.  It
+ * computes the same z as om_ilu_apply (same flags, same DEVICE c128 vectors,
+ * z and v may alias) but takes its scratch -- a complex64 work vector of at
+ * most 1,048,576 rows and a status word -- from a static device array that
+ * every GPU loading the library holds (8 MiB) until the process exits, and
+ * calls no allocator.  Factors with more rows are rejected with OM_EINVAL.
+ * The first call on each device looks up the array's device address (with
+ * that device current); make it before any stream capture.  All calls share
+ * the array: calls whose work overlaps on the GPU race.  Errors: OM_EINVAL,
+ * OM_ETIMEOUT, OM_ECUDA. */
+om_status om_ilu_apply_noalloc(const om_ilu *M, int32_t flags, const double *v, double *z,
+                               void *stream);
 /* <a^dag a>, <b^dag b> of a DEVICE rho (c128 n x n column-major); out HOST double[2]. */
 om_status om_observables(int32_t Nc, int32_t Nm, const double *rho_dev, double out[2],
                          void *stream);
