@@ -110,16 +110,17 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def sweep_traffic(kernel_hash: str):
-    """DRAM bytes per sweep launch from the committed ncu summary, or None if
-    the kernel source changed since the counters were taken."""
+def sweep_traffic_per_entry(kernel_hash: str):
+    """DRAM bytes per stored factor entry of one sweep launch, from the
+    committed ncu summary of the 40,000-row case, or None if the kernel
+    source changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "sweep_traffic.json")
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
     if d.get("sweep_source_hash") != kernel_hash:
         return None
-    return d.get("bytes_per_launch_full_workload")
+    return d.get("dram_bytes_per_factor_entry")
 
 
 # ----------------------------------------------------------------- GPU arm
@@ -217,8 +218,10 @@ def run_omss(args):
     sweep_avg_ms = sweep_ms / max(sweep_n, 1)
     achieved = sweep_bytes / (sweep_ms / 1e3) / 1e9 if sweep_ms > 0 else 0.0
     peak, peak_kind = measured_peaks()
-    khash = source_hash(os.path.join(ROOT, "paper_1411_4356_gb300", "csrc", "sweep.cu"))
-    traffic = sweep_traffic(khash)
+    khash = source_hash(os.path.join(ROOT, "paper_1411_4356_gb300", "csrc", "tilesweep.cu"))
+    per_entry = sweep_traffic_per_entry(khash)
+    # scaled to one launch of this workload by the factor entries it streams
+    traffic = per_entry * (nnz_l + nnz_u_strict) / 2.0 if per_entry else None
     # Krylov bytes per solve: SpMV (c128 value + column, row pointers, x, y),
     # two sweeps, CGS2 over the basis (two passes, each dots + update over j+1 vectors)
     its = s0["iterations"]
@@ -246,7 +249,7 @@ def run_omss(args):
                    "krylov": "FP64 flexible GMRES", "preconditioner": "ILUT, complex64 sweeps",
                    "parallelism": f"replicas x{world}",
                    "l2": "working set (ILU factors) larger than L2; no flush needed"},
-        "roofline": {"bound": "hbm", "kernel": "sweep_one_block (complex64 L and U sweeps)",
+        "roofline": {"bound": "hbm", "kernel": "tile_sweep (complex64 L and U sweeps)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
                      "traffic": traffic, "avg_launch_ms": sweep_avg_ms, "launches": sweep_n,

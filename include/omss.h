@@ -53,7 +53,7 @@ typedef enum {
     OM_ENOCONV = -5,     /* GMRES hit max_iters; the best iterate is still written */
     OM_EBREAKDOWN = -6,  /* Arnoldi breakdown before convergence */
     OM_ENUMERIC = -7,    /* NaN or Inf met in a residual or a factor */
-    OM_ETIMEOUT = -8     /* a device-side wait exceeded wait_timeout_ns */
+    OM_ETIMEOUT = -8     /* a device-side wait exceeded wait_timeout_ns (reserved) */
 } om_status;
 
 /* Parameters of Eq. 1 and Eq. 3 (units of omega_m) and the Fock cutoffs of
@@ -81,7 +81,8 @@ typedef struct {
                                FP32, and the ILU is an approximation far coarser
                                than FP32 rounding); 1: complex128 sweeps */
     double tol;             /* target of eta = ||L x||_inf / (||L||_inf ||x||_inf) */
-    int64_t wait_timeout_ns;/* bound on any device spin-wait (0: 2 s default) */
+    int64_t wait_timeout_ns;/* bound on device spin-waits; the current kernels
+                               synchronise with barriers only, so it is unused */
 } om_solve_opts;
 
 typedef struct {
@@ -133,9 +134,13 @@ om_status om_permute(const om_matrix *A, void *stream, int32_t *perm_dev, om_mat
  * 1e-14 ||row i||_inf is replaced by that value and counted.
  * flags bit 0: add the moduli of the entries dropped from row i to |u_ii|
  * (diagonal compensation); bit 1: also store the conjugate transposes U^H,
- * L^H needed by the adjoint.  Rows are factored in parallel on the host
- * cores (OMSS_ILU_THREADS caps the thread count); the factors are identical
- * to those of the serial row order.  Errors: OM_EINVAL, OM_ENOMEM. */
+ * L^H needed by the adjoint; bit 2: also keep complex128 sweep data (the
+ * sweeps use complex64 otherwise).  Rows are factored in parallel on the
+ * host cores (OMSS_ILU_THREADS caps the thread count); the factors are
+ * identical to those of the serial row order.  On the device the factors are
+ * stored in the tiled form of the sweeps: per tile of 32 rows, the dense
+ * inverse of the diagonal block and the entries that reach earlier tiles.
+ * Errors: OM_EINVAL, OM_ENOMEM. */
 om_status om_ilu_factor(const om_matrix *A_rcm, double droptol, double fill, int32_t flags,
                         void *stream, om_ilu **out);
 
@@ -173,8 +178,9 @@ om_status om_steady_state_adjoint(const om_matrix *A_rcm, const om_ilu *M, const
  * y = A x (DEVICE c128 vectors of length nrows). */
 om_status om_spmv(const om_matrix *A, const double *x, double *y, void *stream);
 /* z = (L U)^{-1} v, or (L U)^{-H} v, with DEVICE c128[N] vectors (z and v may
- * alias).  flags bit 0: sweep with the complex128 factors (else complex64);
- * bit 1: apply the conjugate transpose.  Errors: OM_EINVAL, OM_ETIMEOUT. */
+ * alias).  flags bit 0: sweep with the complex128 data (the factor must have
+ * been built with it), else complex64; bit 1: apply the conjugate transpose
+ * (the factor must keep the transposes).  Errors: OM_EINVAL, OM_ECUDA. */
 om_status om_ilu_apply(const om_ilu *M, int32_t flags, const double *v, double *z,
                        void *stream);
 /* Allocation-free variant of om_ilu_apply.  The paper has no counterpart:
@@ -190,7 +196,7 @@ om_status om_ilu_apply(const om_ilu *M, int32_t flags, const double *v, double *
  * The first call on each device looks up the array's device address (with
  * that device current); make it before any stream capture.  All calls share
  * the array: calls whose work overlaps on the GPU race.  Errors: OM_EINVAL,
- * OM_ETIMEOUT, OM_ECUDA. */
+ * OM_ECUDA. */
 om_status om_ilu_apply_noalloc(const om_ilu *M, int32_t flags, const double *v, double *z,
                                void *stream);
 /* <a^dag a>, <b^dag b> of a DEVICE rho (c128 n x n column-major); out HOST double[2]. */

@@ -123,12 +123,14 @@ def permute(A: Matrix, stream=None):
 
 
 def ilu_factor(A: Matrix, droptol: float, fill: float, compensate: bool = False, adjoint: bool = False,
-               stream=None) -> ILU:
+               fp64_sweeps: bool = False, stream=None) -> ILU:
     """Sec. II: ILUT(droptol, fill) of a permuted matrix; adjoint=True also keeps
-    the conjugate-transposed factors for the adjoint sweeps."""
+    the conjugate-transposed factors for the adjoint sweeps, fp64_sweeps=True
+    the complex128 sweep data."""
     lib = _lib.load()
     out = ctypes.c_void_p()
-    check(lib.om_ilu_factor(A.handle, float(droptol), float(fill), (1 if compensate else 0) | (2 if adjoint else 0),
+    flags = (1 if compensate else 0) | (2 if adjoint else 0) | (4 if fp64_sweeps else 0)
+    check(lib.om_ilu_factor(A.handle, float(droptol), float(fill), flags,
                             ctypes.c_void_p(_stream(stream)), ctypes.byref(out)), "om_ilu_factor")
     return ILU(out.value, A.nnz)
 

@@ -1,0 +1,49 @@
+"""Named small cases for profiling single kernels (ncu captures).
+
+    python -m paper_1411_4356_gb300.cases sweep_10x20
+
+builds the 40,000-row Liouvillian (N_c = 10, N_m = 20, the 360,000-row
+system's parameters), permutes it, factors it (d = 1e-5, p = 100) and runs
+the complex64 preconditioner solve three times; `spmv_10x20` runs the SpMV
+three times instead.  Inputs are larger than L2 (the factors are ~0.4 GB).
+"""
+from __future__ import annotations
+
+import sys
+
+import torch
+
+from . import api
+from .workloads import MID
+
+
+def _system(Nc, Nm):
+    p = MID.params.with_(Nc=Nc, Nm=Nm)
+    A = api.build_liouvillian(p)
+    Ar, perm = api.permute(A)
+    return p, Ar, perm
+
+
+def sweep(Nc=10, Nm=20):
+    p, Ar, perm = _system(Nc, Nm)
+    M = api.ilu_factor(Ar, MID.droptol, MID.fill)
+    x = torch.randn(Ar.N, dtype=torch.complex128, device="cuda")
+    for _ in range(3):
+        api.ilu_apply(M, x)
+    torch.cuda.synchronize()
+    print(f"sweep case: rows {Ar.N}, nnz(L) {M.nnz_l}, nnz(U) {M.nnz_u}, levels {M.levels_l}/{M.levels_u}")
+
+
+def spmv(Nc=10, Nm=60):
+    p, Ar, perm = _system(Nc, Nm)
+    x = torch.randn(Ar.N, dtype=torch.complex128, device="cuda")
+    for _ in range(3):
+        api.spmv(Ar, x)
+    torch.cuda.synchronize()
+    print(f"spmv case: rows {Ar.N}, nnz {Ar.nnz}")
+
+
+CASES = {"sweep_10x20": lambda: sweep(10, 20), "spmv_10x60": lambda: spmv(10, 60)}
+
+if __name__ == "__main__":
+    CASES[sys.argv[1]]()

@@ -150,36 +150,32 @@ struct om_matrix {
     ~om_matrix();
 };
 
-// One triangular factor in CSR (strict part) plus optional inverse diagonal.
-struct om_tri {
-    int64_t N = 0, nnz = 0;
-    omss::DBuf<int64_t> rowptr;
-    omss::DBuf<int32_t> col;
-    omss::DBuf<double2> val;
-    omss::DBuf<float2> val32;     // complex64 copy (mixed precision)
-    int64_t levels = 0;           // depth of the dependency DAG
-    void release(cudaStream_t s) {
-        rowptr.release(s);
-        col.release(s);
-        val.release(s);
-        val32.release(s);
-    }
+// Tiled form of one triangular factor for the sweeps (tilesweep.cu): rows in
+// sweep order t in tiles of 32; per tile the entries reaching earlier tiles
+// in sliced-ELL layout (slot-major, 32 rows per slot, zero-padded) and the
+// dense inverse of the 32 x 32 diagonal block (column-major).
+struct TilePlan {
+    int64_t N = 0, ntiles = 0, padded_entries = 0;
+    bool forward = true;
+    omss::DBuf<int64_t> tile_ptr;  // ntiles + 1 offsets into col / val
+    omss::DBuf<int32_t> col;       // sweep-order column t_j
+    omss::DBuf<float2> val32;      // complex64 values
+    omss::DBuf<double2> val64;     // complex128 values (optional)
+    omss::DBuf<float2> G32;        // complex64 inverses, ntiles x 32 x 32
+    omss::DBuf<double2> G64;       // complex128 inverses (optional)
+    void release(cudaStream_t s);
 };
 
 struct om_ilu {
     int64_t N = 0;
-    om_tri L;        // strict lower part of the unit lower factor
-    om_tri U;        // strict upper part of U
-    omss::DBuf<double2> dinv;   // 1 / u_ii
-    omss::DBuf<double2> dinvh;  // 1 / conj(u_ii), diagonal of U^H inverted
-    omss::DBuf<float2> dinv32;
-    omss::DBuf<float2> dinvh32;
-    // conjugate transposes, stored as CSR of U^H (strict lower) and L^H (strict upper)
-    om_tri UH;
-    om_tri LH;
+    int64_t nnz_l = 0;         // strict L entries
+    int64_t nnz_u = 0;         // U entries including the diagonal
+    int64_t levels_l = 0, levels_u = 0;  // depths of the dependency DAGs
+    TilePlan L, U;             // forward L (unit), backward U
+    TilePlan UH, LH;           // conjugate transposes: forward U^H, backward L^H (unit)
     int64_t n_guarded = 0;
     bool has_transpose = false;
-    omss::DBuf<int> status;     // device status word for bounded waits
+    bool has_fp64 = false;
     cudaStream_t owner_stream = nullptr;
     ~om_ilu();
 };
@@ -192,17 +188,14 @@ void spmv_c128(const int64_t *rowptr, const int32_t *col, const double2 *val, in
 void spmv_c64(const int64_t *rowptr, const int32_t *col, const float2 *val, int64_t N,
               const float2 *x, float2 *y, cudaStream_t s);
 
-// z = T^{-1} v for a triangular factor; lower: forward rows 0..N-1, else
-// backward; dinv == nullptr means unit diagonal.  v and z may alias.
-void sweep_c128(const om_tri &T, bool lower, const double2 *dinv, const double2 *v, double2 *z,
-                int *status, int64_t timeout_ns, cudaStream_t s);
-void sweep_c64(const om_tri &T, bool lower, const float2 *dinv, const float2 *v, float2 *z,
-               int *status, int64_t timeout_ns, cudaStream_t s);
+// Tiled sweeps z = T^{-1} v in natural order (v and z may alias).
+void tile_sweep_c64(const TilePlan &P, const float2 *v, float2 *z, cudaStream_t s);
+void tile_sweep_c128(const TilePlan &P, const double2 *v, double2 *z, cudaStream_t s);
 
 // z = M^{-1} v (or M^{-H} v) with complex128 vectors; fp64 selects complex128
 // sweeps, otherwise the complex64 factors are used through tmp32 (N entries).
 void precond_apply(const om_ilu &M, bool conj_transpose, bool fp64, const double2 *v, double2 *z,
-                   float2 *tmp32, int64_t timeout_ns, cudaStream_t s);
+                   float2 *tmp32, cudaStream_t s);
 void to_c64(const double2 *v, int64_t N, float2 *out, cudaStream_t s);
 void to_c128(const float2 *v, int64_t N, double2 *out, cudaStream_t s);
 

@@ -12,11 +12,10 @@
 // below 1e-14 ||row i||_inf is replaced by that value and counted.
 //
 // The factorisation runs on the host cores (it is the setup stage of the
-// method; the paper runs it serially), row-parallel over all cores; the
-// factors are then laid out on the device for the sweeps:
-// strict L, strict U and 1/u_ii in CSR (int64 row pointers, int32 columns,
-// c128 values), plus complex64 copies and the conjugate transposes U^H, L^H
-// used by the adjoint.
+// method; the paper runs it serially), row-parallel over all cores.  The
+// factors then go to the device in the tiled form of the sweeps
+// (tilesweep.cu): complex64 always, complex128 on request, and the
+// conjugate transposes U^H, L^H when the adjoint needs them.
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -265,29 +264,11 @@ int64_t dag_depth(int64_t N, const HostTri &T, bool lower) {
     return N ? best + 1 : 0;
 }
 
-void upload(om_tri &D, int64_t N, const HostTri &T, bool want32, cudaStream_t s) {
-    D.N = N;
-    D.nnz = (int64_t)T.ci.size();
-    D.rowptr.alloc(N + 1, s);
-    D.col.alloc(std::max<int64_t>(D.nnz, 1), s);
-    D.val.alloc(std::max<int64_t>(D.nnz, 1), s);
-    OM_CUDA_TRY(cudaMemcpyAsync(D.rowptr.p, T.rp.data(), sizeof(int64_t) * (N + 1), cudaMemcpyHostToDevice, s));
-    if (D.nnz) {
-        OM_CUDA_TRY(cudaMemcpyAsync(D.col.p, T.ci.data(), sizeof(int32_t) * D.nnz, cudaMemcpyHostToDevice, s));
-        static_assert(sizeof(cd) == sizeof(double2), "complex layout");
-        OM_CUDA_TRY(cudaMemcpyAsync(D.val.p, T.va.data(), sizeof(double2) * D.nnz, cudaMemcpyHostToDevice, s));
-    }
-    if (want32) {
-        std::vector<float2> v32(T.va.size());
-        for (size_t t = 0; t < T.va.size(); ++t) v32[t] = make_float2((float)T.va[t].real(), (float)T.va[t].imag());
-        D.val32.alloc(std::max<int64_t>(D.nnz, 1), s);
-        if (D.nnz)
-            OM_CUDA_TRY(cudaMemcpyAsync(D.val32.p, v32.data(), sizeof(float2) * D.nnz, cudaMemcpyHostToDevice, s));
-        OM_CUDA_TRY(cudaStreamSynchronize(s));
-    }
-}
-
 }  // namespace
+
+void build_tile_plan(TilePlan &P, int64_t N, const std::vector<int64_t> &rp, const std::vector<int32_t> &ci,
+                     const std::vector<cd> &va, const cd *diag, bool forward, bool want64, cudaStream_t s);
+
 }  // namespace omss
 
 using namespace omss;
@@ -298,11 +279,6 @@ om_ilu::~om_ilu() {
     U.release(s);
     UH.release(s);
     LH.release(s);
-    dinv.release(s);
-    dinvh.release(s);
-    dinv32.release(s);
-    dinvh32.release(s);
-    status.release(s);
 }
 
 extern "C" om_status om_ilu_factor(const om_matrix *A, double droptol, double fill, int32_t flags,
@@ -325,40 +301,22 @@ extern "C" om_status om_ilu_factor(const om_matrix *A, double droptol, double fi
         M->owner_stream = s;
         M->N = N;
         M->n_guarded = guarded_count;
-        upload(M->L, N, L, true, s);
-        upload(M->U, N, U, true, s);
-        M->L.levels = dag_depth(N, L, true);
-        M->U.levels = dag_depth(N, U, false);
-        HostTri UH, LH;
+        M->nnz_l = (int64_t)L.ci.size();
+        M->nnz_u = (int64_t)U.ci.size() + N;
+        M->levels_l = dag_depth(N, L, true);
+        M->levels_u = dag_depth(N, U, false);
+        const bool want64 = (flags & 4) != 0;
+        M->has_fp64 = want64;
+        build_tile_plan(M->L, N, L.rp, L.ci, L.va, nullptr, true, want64, s);
+        build_tile_plan(M->U, N, U.rp, U.ci, U.va, diag.data(), false, want64, s);
         if (flags & 2) {  // conjugate transposes for the adjoint sweeps
-            UH = conj_transpose(N, U);
-            LH = conj_transpose(N, L);
-            upload(M->UH, N, UH, true, s);
-            upload(M->LH, N, LH, true, s);
-            M->UH.levels = M->U.levels;
-            M->LH.levels = M->L.levels;
+            HostTri UH = conj_transpose(N, U), LH = conj_transpose(N, L);
+            std::vector<cd> diagh(N);
+            for (int64_t i = 0; i < N; ++i) diagh[i] = std::conj(diag[i]);
+            build_tile_plan(M->UH, N, UH.rp, UH.ci, UH.va, diagh.data(), true, want64, s);
+            build_tile_plan(M->LH, N, LH.rp, LH.ci, LH.va, nullptr, false, want64, s);
             M->has_transpose = true;
         }
-        std::vector<double2> dinv(N);
-        std::vector<double2> dinvh(N);
-        std::vector<float2> dinv32(N), dinvh32(N);
-        for (int64_t i = 0; i < N; ++i) {
-            cd r = 1.0 / diag[i];
-            dinv[i] = make_double2(r.real(), r.imag());
-            dinvh[i] = make_double2(r.real(), -r.imag());
-            dinv32[i] = make_float2((float)r.real(), (float)r.imag());
-            dinvh32[i] = make_float2((float)r.real(), -(float)r.imag());
-        }
-        M->dinv.alloc(N, s);
-        M->dinv32.alloc(N, s);
-        M->dinvh.alloc(N, s);
-        M->dinvh32.alloc(N, s);
-        OM_CUDA_TRY(cudaMemcpyAsync(M->dinvh32.p, dinvh32.data(), sizeof(float2) * N, cudaMemcpyHostToDevice, s));
-        OM_CUDA_TRY(cudaMemcpyAsync(M->dinvh.p, dinvh.data(), sizeof(double2) * N, cudaMemcpyHostToDevice, s));
-        OM_CUDA_TRY(cudaMemcpyAsync(M->dinv.p, dinv.data(), sizeof(double2) * N, cudaMemcpyHostToDevice, s));
-        OM_CUDA_TRY(cudaMemcpyAsync(M->dinv32.p, dinv32.data(), sizeof(float2) * N, cudaMemcpyHostToDevice, s));
-        M->status.alloc(4, s);
-        OM_CUDA_TRY(cudaMemsetAsync(M->status.p, 0, sizeof(int) * 4, s));
         OM_CUDA_TRY(cudaStreamSynchronize(s));
         *out = M.release();
     });
@@ -368,10 +326,10 @@ extern "C" om_status om_ilu_info(const om_ilu *M, int64_t *nnz_l, int64_t *nnz_u
                                  int64_t *levels_l, int64_t *levels_u) {
     return guarded([&] {
         OM_REQUIRE(M, "om_ilu_info: NULL handle");
-        if (nnz_l) *nnz_l = M->L.nnz;
-        if (nnz_u) *nnz_u = M->U.nnz + M->N;  // diagonal of U included
+        if (nnz_l) *nnz_l = M->nnz_l;
+        if (nnz_u) *nnz_u = M->nnz_u;  // diagonal of U included
         if (n_guarded) *n_guarded = M->n_guarded;
-        if (levels_l) *levels_l = M->L.levels;
-        if (levels_u) *levels_u = M->U.levels;
+        if (levels_l) *levels_l = M->levels_l;
+        if (levels_u) *levels_u = M->levels_u;
     });
 }

@@ -80,14 +80,13 @@ __global__ void observables_kernel(int Nc, int Nm, const double2 *rho, double *o
 struct ForwardOps : KrylovOps {
     const om_matrix *A;
     const om_ilu *M;
-    int64_t timeout;
     bool fp64_precond;
     float2 *tmp32;
     void apply(const double2 *v, double2 *out, cudaStream_t s) override {
         spmv_c128(A->rowptr.p, A->col.p, A->val.p, A->N, v, out, s);
     }
     void precond(const double2 *v, double2 *out, cudaStream_t s) override {
-        precond_apply(*M, false, fp64_precond, v, out, tmp32, timeout, s);
+        precond_apply(*M, false, fp64_precond, v, out, tmp32, s);
     }
 };
 
@@ -163,11 +162,9 @@ extern "C" om_status om_steady_state_solve(const om_matrix *A, const om_ilu *M, 
         OM_CHECK_LAUNCH();
         if (x0) dev_copy(reinterpret_cast<const double2 *>(x0), x.p, N, s);
         else dev_zero(x.p, N, s);
-        OM_CUDA_TRY(cudaMemsetAsync(M->status.p, 0, sizeof(int), s));
         ForwardOps ops;
         ops.A = A;
         ops.M = M;
-        ops.timeout = opts->wait_timeout_ns;
         ops.fp64_precond = opts->precond_fp64 != 0;
         ops.tmp32 = W.tmp32.p;
         om_solve_info inf{};
@@ -182,13 +179,6 @@ extern "C" om_status om_steady_state_solve(const om_matrix *A, const om_ilu *M, 
             eta = eta_of(*A, x.p, W.w.p, W, s);
             xinf = dev_maxabs(x.p, N, W, s);
             if (cycles <= 64) inf.residual_history[cycles - 1] = eta;
-            int timed_out = 0;
-            OM_CUDA_TRY(cudaMemcpyAsync(&timed_out, M->status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-            OM_CUDA_TRY(cudaStreamSynchronize(s));
-            if (timed_out) {
-                final_status = OM_ETIMEOUT;
-                break;
-            }
             if (!std::isfinite(eta)) {
                 final_status = OM_ENUMERIC;
                 break;
@@ -223,22 +213,18 @@ extern "C" om_status om_steady_state_solve(const om_matrix *A, const om_ilu *M, 
 }
 
 extern "C" om_status om_ilu_apply(const om_ilu *M, int32_t flags, const double *v, double *z, void *stream) {
-    const int32_t conj_transpose = flags & 2 ? 1 : 0;
     return guarded([&] {
         OM_REQUIRE(M && v && z, "om_ilu_apply: NULL argument");
-        OM_REQUIRE(!(flags & 2) || M->has_transpose, "om_ilu_apply: factor built without conjugate transposes");
+        const bool conj_transpose = (flags & 2) != 0, fp64 = (flags & 1) != 0;
+        OM_REQUIRE(!conj_transpose || M->has_transpose, "om_ilu_apply: factor built without conjugate transposes");
+        OM_REQUIRE(!fp64 || M->has_fp64, "om_ilu_apply: factor built without complex128 sweep data");
         cudaStream_t s = as_stream(stream);
-        const double2 *vv = reinterpret_cast<const double2 *>(v);
-        double2 *zz = reinterpret_cast<double2 *>(z);
-        OM_CUDA_TRY(cudaMemsetAsync(M->status.p, 0, sizeof(int), s));
         DBuf<float2> tmp;
-        tmp.alloc(M->N, s);
-        precond_apply(*M, conj_transpose != 0, (flags & 1) != 0, vv, zz, tmp.p, 0, s);
+        if (!fp64) tmp.alloc(M->N, s);
+        precond_apply(*M, conj_transpose, fp64, reinterpret_cast<const double2 *>(v), reinterpret_cast<double2 *>(z),
+                      tmp.p, s);
         tmp.release(s);
-        int flag = 0;
-        OM_CUDA_TRY(cudaMemcpyAsync(&flag, M->status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         OM_CUDA_TRY(cudaStreamSynchronize(s));
-        if (flag) throw Error{OM_ETIMEOUT, "triangular sweep wait timed out"};
     });
 }
 

@@ -1,0 +1,359 @@
+// K6 / K7: triangular sweeps with the ILU factors -- the preconditioner solve
+// of Eq. 6, M^{-1} v = U^{-1} (L^{-1} v), and its conjugate transpose for the
+// adjoint -- as a block-synchronous tiled sweep.
+//
+// After RCM and ILUT fill, the factors' dependency DAG is close to a chain
+// (tens of thousands of levels at 360,000 rows), so row-level parallelism is
+// scarce and every dependency hop costs latency.  This sweep removes the
+// hops inside a tile instead of chasing them:
+//
+//  * Rows are taken in sweep order t (t = r forward, t = N-1-r backward) in
+//    tiles of 32.  For tile T the system is D_T x_T = v_T - E_T x_<T, where
+//    D_T is the 32 x 32 lower-triangular diagonal block (diagonal 1 or u_rr)
+//    and E_T holds the entries that reach earlier tiles.
+//  * Setup stores G_T = D_T^{-1} (dense, computed in FP64 on the host cores)
+//    and E_T in a sliced-ELL layout per tile (slot k of the 32 rows is
+//    contiguous, padded with zero entries).
+//  * One thread block runs the tiles in order.  Phase A: all 16 warps share
+//    the slots of E_T (each a contiguous run, loaded eight slots at a time so
+//    the loads overlap), each lane owning one row, and leave partial sums in
+//    shared memory; earlier x values come from a shared-memory ring of WIN
+//    rows or, when older, from global memory.  Phase B: warp 0 forms
+//    y = v_T - E_T x and x_T = G_T y with 32 warp shuffles, then writes x_T.
+//    A __syncthreads separates the phases; nothing spins.
+//  * The next tiles' data is prefetched into L2 with cp.async.bulk.prefetch.
+//
+// A tile's 32 rows thus cost one barrier round instead of up to 32 dependent
+// hops; the sweep is bounded by the bandwidth one SM can draw and by the
+// per-tile barrier latency.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <thread>
+
+#include "common.cuh"
+
+namespace omss {
+namespace {
+
+constexpr int kTile = 32;
+constexpr int kTileWarps = 16;
+
+template <class CT>
+struct TOps;
+template <>
+struct TOps<double2> {
+    __device__ static double2 zero() { return make_double2(0, 0); }
+    __device__ static double2 fma(double2 a, double2 x, double2 acc) {
+        return make_double2(__fma_rn(a.x, x.x, __fma_rn(-a.y, x.y, acc.x)), __fma_rn(a.x, x.y, __fma_rn(a.y, x.x, acc.y)));
+    }
+    __device__ static double2 sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+    __device__ static double2 add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+};
+template <>
+struct TOps<float2> {
+    __device__ static float2 zero() { return make_float2(0, 0); }
+    __device__ static float2 fma(float2 a, float2 x, float2 acc) {
+        return make_float2(__fmaf_rn(a.x, x.x, __fmaf_rn(-a.y, x.y, acc.x)), __fmaf_rn(a.x, x.y, __fmaf_rn(a.y, x.x, acc.y)));
+    }
+    __device__ static float2 sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+    __device__ static float2 add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+};
+
+__device__ inline void prefetch_l2(const void *p, uint32_t bytes) {
+    // bulk prefetch of a contiguous range into L2 (16-byte aligned, multiple of 16 bytes)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+__device__ inline void prefetch_range(const void *base, size_t elem, int64_t begin, int64_t end) {
+    // align the byte range to 16 bytes and split it into pieces below 1 MiB
+    uintptr_t lo = (reinterpret_cast<uintptr_t>(base) + (uintptr_t)begin * elem) & ~uintptr_t(15);
+    uintptr_t hi = (reinterpret_cast<uintptr_t>(base) + (uintptr_t)end * elem + 15) & ~uintptr_t(15);
+    while (lo < hi) {
+        const uintptr_t rest = hi - lo;
+        const uint32_t n = (uint32_t)(rest < (uintptr_t(1) << 19) ? rest : (uintptr_t(1) << 19));
+        prefetch_l2(reinterpret_cast<const void *>(lo), n);
+        lo += n;
+    }
+}
+
+// v, z: natural-order vectors (index r); the tile data is in sweep order t.
+template <class CT, int WIN>
+__global__ void __launch_bounds__(kTileWarps * 32, 1)
+tile_sweep(int64_t N, int64_t ntiles, int forward, const int64_t *__restrict__ tile_ptr,
+           const int32_t *__restrict__ scol, const CT *__restrict__ sval, const CT *__restrict__ G,
+           const CT *v, CT *z) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CT *win = reinterpret_cast<CT *>(smem_raw);                      // WIN rows of x, by t
+    CT *part = win + WIN;                                              // kTileWarps x 32 partial sums
+    CT *gs = part + kTileWarps * kTile;                                // 32 x 32 inverse of the tile
+    using O = TOps<CT>;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        for (int64_t q = 0; q < 2 && q < ntiles; ++q)
+            prefetch_range(scol, sizeof(int32_t), tile_ptr[q], tile_ptr[q + 1]),
+                prefetch_range(sval, sizeof(CT), tile_ptr[q], tile_ptr[q + 1]);
+    }
+    for (int64_t T = 0; T < ntiles; ++T) {
+        const int64_t t0 = T * kTile;
+        const int64_t b = tile_ptr[T], e = tile_ptr[T + 1];
+        const int64_t width = (e - b) / kTile;
+        if (threadIdx.x == 0 && T + 2 < ntiles) {
+            prefetch_range(scol, sizeof(int32_t), tile_ptr[T + 2], tile_ptr[T + 3]);
+            prefetch_range(sval, sizeof(CT), tile_ptr[T + 2], tile_ptr[T + 3]);
+            prefetch_range(G, sizeof(CT), (T + 2) * kTile * kTile, (T + 3) * kTile * kTile);
+        }
+        // issue the loads of G_T (column-major) and v_T now; they are consumed
+        // after phase A, so their latency overlaps it
+        constexpr int kGPerThread = kTile * kTile / (kTileWarps * 32);
+        CT greg[kGPerThread];
+#pragma unroll
+        for (int q = 0; q < kGPerThread; ++q) greg[q] = __ldcs(G + T * kTile * kTile + q * blockDim.x + threadIdx.x);
+        CT vreg = O::zero();
+        if (warp == 0 && t0 + lane < N) vreg = __ldcg(v + (forward ? t0 + lane : N - 1 - (t0 + lane)));
+        // phase A: warp w takes a contiguous run of the slots of E_T; loads are
+        // batched eight deep so that their latencies overlap
+        const int64_t per = (width + kTileWarps - 1) / kTileWarps;
+        const int64_t k0 = warp * per, k1 = (k0 + per < width) ? k0 + per : width;
+        CT acc = O::zero(), acc2 = O::zero();
+        auto gather = [&](int32_t tj) -> CT {
+            return (t0 - tj <= WIN - kTile) ? win[tj & (WIN - 1)] : __ldcg(z + (forward ? tj : N - 1 - tj));
+        };
+        int64_t k = k0;
+        for (; k + 8 <= k1; k += 8) {
+            int32_t tj[8];
+            CT a[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t idx = b + (k + u) * kTile + lane;
+                tj[u] = __ldcs(scol + idx);
+                a[u] = __ldcs(sval + idx);
+            }
+            CT xs[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) xs[u] = gather(tj[u]);
+#pragma unroll
+            for (int u = 0; u < 8; u += 2) {
+                acc = O::fma(a[u], xs[u], acc);
+                acc2 = O::fma(a[u + 1], xs[u + 1], acc2);
+            }
+        }
+        for (; k < k1; ++k) {
+            const int64_t idx = b + k * kTile + lane;
+            acc = O::fma(__ldcs(sval + idx), gather(__ldcs(scol + idx)), acc);
+        }
+        acc = O::add(acc, acc2);
+        part[warp * kTile + lane] = acc;
+#pragma unroll
+        for (int q = 0; q < kGPerThread; ++q) gs[q * blockDim.x + threadIdx.x] = greg[q];
+        __syncthreads();
+        // phase B: x_T = G_T (v_T - sum of partials)
+        if (warp == 0) {
+            const int64_t t = t0 + lane;
+            const int64_t r = forward ? t : N - 1 - t;
+            CT y = O::zero();
+            if (t < N) {
+                y = vreg;
+                for (int w = 0; w < kTileWarps; ++w) y = O::sub(y, part[w * kTile + lane]);
+            }
+            CT x = O::zero();
+#pragma unroll 8
+            for (int c = 0; c < kTile; ++c) {
+                CT yc;
+                yc.x = __shfl_sync(0xffffffffu, y.x, c);
+                yc.y = __shfl_sync(0xffffffffu, y.y, c);
+                x = O::fma(gs[c * kTile + lane], yc, x);
+            }
+            if (t < N) {
+                win[t & (WIN - 1)] = x;
+                z[r] = x;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+namespace {
+using cd = std::complex<double>;
+}
+
+// Builds the tiled form of a strict triangular factor T (CSR over rows r):
+// forward (lower, rows in increasing r) or backward (upper, decreasing r);
+// diag == nullptr means a unit diagonal.
+void build_tile_plan(TilePlan &P, int64_t N, const std::vector<int64_t> &rp, const std::vector<int32_t> &ci,
+                     const std::vector<cd> &va, const cd *diag, bool forward, bool want64, cudaStream_t s) {
+    P.N = N;
+    P.forward = forward;
+    const int64_t ntiles = (N + kTile - 1) / kTile;
+    P.ntiles = ntiles;
+    auto tmap = [&](int64_t idx) { return forward ? idx : N - 1 - idx; };
+    // widths of the external (earlier-tile) part per tile
+    std::vector<int64_t> tptr(ntiles + 1, 0);
+    for (int64_t T = 0; T < ntiles; ++T) {
+        int64_t wmax = 0;
+        const int64_t t0 = T * kTile;
+        for (int64_t t = t0; t < std::min(N, t0 + kTile); ++t) {
+            const int64_t r = tmap(t);
+            int64_t cnt = 0;
+            for (int64_t q = rp[r]; q < rp[r + 1]; ++q)
+                if (tmap(ci[q]) < t0) ++cnt;
+            wmax = std::max(wmax, cnt);
+        }
+        tptr[T + 1] = tptr[T] + wmax * kTile;
+    }
+    const int64_t total = tptr[ntiles];
+    std::vector<int32_t> scol(std::max<int64_t>(total, 1), 0);
+    std::vector<cd> sval(std::max<int64_t>(total, 1), cd(0, 0));
+    std::vector<cd> G((size_t)ntiles * kTile * kTile, cd(0, 0));
+    auto work = [&](int64_t Tb, int64_t Te) {
+        std::vector<cd> D(kTile * kTile), Gl(kTile * kTile);
+        for (int64_t T = Tb; T < Te; ++T) {
+            const int64_t t0 = T * kTile;
+            const int64_t width = (tptr[T + 1] - tptr[T]) / kTile;
+            std::fill(D.begin(), D.end(), cd(0, 0));
+            for (int a = 0; a < kTile; ++a) {
+                const int64_t t = t0 + a;
+                if (t >= N) {
+                    D[a * kTile + a] = 1.0;
+                    continue;
+                }
+                const int64_t r = tmap(t);
+                D[a * kTile + a] = diag ? diag[r] : cd(1, 0);
+                int64_t k = 0;
+                for (int64_t q = rp[r]; q < rp[r + 1]; ++q) {
+                    const int64_t tj = tmap(ci[q]);
+                    if (tj < t0) {
+                        const int64_t idx = tptr[T] + k * kTile + a;
+                        scol[idx] = (int32_t)tj;
+                        sval[idx] = va[q];
+                        ++k;
+                    } else {
+                        D[a * kTile + (tj - t0)] = va[q];
+                    }
+                }
+                (void)width;
+            }
+            // G = D^{-1} by forward substitution, column by column (FP64)
+            std::fill(Gl.begin(), Gl.end(), cd(0, 0));
+            for (int c = 0; c < kTile; ++c) {
+                for (int a = c; a < kTile; ++a) {
+                    cd sacc = (a == c) ? cd(1, 0) : cd(0, 0);
+                    for (int q = c; q < a; ++q) sacc -= D[a * kTile + q] * Gl[q * kTile + c];
+                    Gl[a * kTile + c] = sacc / D[a * kTile + a];
+                }
+            }
+            // column-major for the device: G[T][c][a]
+            for (int c = 0; c < kTile; ++c)
+                for (int a = 0; a < kTile; ++a) G[(size_t)T * kTile * kTile + c * kTile + a] = Gl[a * kTile + c];
+        }
+    };
+    unsigned nt = std::max(1u, std::thread::hardware_concurrency());
+    if ((int64_t)nt > ntiles) nt = (unsigned)std::max<int64_t>(1, ntiles);
+    std::vector<std::thread> pool;
+    const int64_t chunk = (ntiles + nt - 1) / nt;
+    for (unsigned q = 0; q < nt; ++q) {
+        int64_t Tb = q * chunk, Te = std::min(ntiles, Tb + chunk);
+        if (Tb < Te) pool.emplace_back(work, Tb, Te);
+    }
+    for (auto &th : pool) th.join();
+
+    std::vector<float2> sval32(sval.size()), G32(G.size());
+    for (size_t q = 0; q < sval.size(); ++q) sval32[q] = make_float2((float)sval[q].real(), (float)sval[q].imag());
+    for (size_t q = 0; q < G.size(); ++q) G32[q] = make_float2((float)G[q].real(), (float)G[q].imag());
+    P.tile_ptr.alloc(ntiles + 1, s);
+    P.col.alloc(scol.size(), s);
+    P.val32.alloc(sval32.size(), s);
+    P.G32.alloc(std::max<size_t>(G32.size(), 1), s);
+    OM_CUDA_TRY(cudaMemcpyAsync(P.tile_ptr.p, tptr.data(), sizeof(int64_t) * (ntiles + 1), cudaMemcpyHostToDevice, s));
+    OM_CUDA_TRY(cudaMemcpyAsync(P.col.p, scol.data(), sizeof(int32_t) * scol.size(), cudaMemcpyHostToDevice, s));
+    OM_CUDA_TRY(cudaMemcpyAsync(P.val32.p, sval32.data(), sizeof(float2) * sval32.size(), cudaMemcpyHostToDevice, s));
+    if (!G32.empty())
+        OM_CUDA_TRY(cudaMemcpyAsync(P.G32.p, G32.data(), sizeof(float2) * G32.size(), cudaMemcpyHostToDevice, s));
+    if (want64) {
+        P.val64.alloc(sval.size(), s);
+        P.G64.alloc(std::max<size_t>(G.size(), 1), s);
+        OM_CUDA_TRY(cudaMemcpyAsync(P.val64.p, sval.data(), sizeof(double2) * sval.size(), cudaMemcpyHostToDevice, s));
+        if (!G.empty())
+            OM_CUDA_TRY(cudaMemcpyAsync(P.G64.p, G.data(), sizeof(double2) * G.size(), cudaMemcpyHostToDevice, s));
+    }
+    P.padded_entries = total;
+    OM_CUDA_TRY(cudaStreamSynchronize(s));  // host staging vectors go out of scope
+}
+
+__global__ void narrow(const double2 *__restrict__ v, int64_t N, float2 *__restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride)
+        out[i] = make_float2((float)v[i].x, (float)v[i].y);
+}
+__global__ void widen(const float2 *__restrict__ v, int64_t N, double2 *__restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride)
+        out[i] = make_double2((double)v[i].x, (double)v[i].y);
+}
+
+void to_c64(const double2 *v, int64_t N, float2 *out, cudaStream_t s) {
+    int64_t need = (N + 255) / 256;
+    unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 4));
+    narrow<<<blocks, 256, 0, s>>>(v, N, out);
+    omss::note_launch();
+    OM_CHECK_LAUNCH();
+}
+void to_c128(const float2 *v, int64_t N, double2 *out, cudaStream_t s) {
+    int64_t need = (N + 255) / 256;
+    unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 4));
+    widen<<<blocks, 256, 0, s>>>(v, N, out);
+    omss::note_launch();
+    OM_CHECK_LAUNCH();
+}
+
+template <class CT, int WIN>
+static void launch_tile(const TilePlan &P, const CT *val, const CT *G, const CT *v, CT *z, cudaStream_t s) {
+    if (P.ntiles == 0) return;
+    const size_t smem = sizeof(CT) * (WIN + kTileWarps * kTile + kTile * kTile);
+    auto k = tile_sweep<CT, WIN>;
+    OM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ProfScope prof(PROF_SWEEP, s);
+    k<<<1, kTileWarps * 32, smem, s>>>(P.N, P.ntiles, P.forward ? 1 : 0, P.tile_ptr.p, P.col.p, val, G, v, z);
+    omss::note_launch();
+    OM_CHECK_LAUNCH();
+}
+
+void tile_sweep_c64(const TilePlan &P, const float2 *v, float2 *z, cudaStream_t s) {
+    launch_tile<float2, 16384>(P, P.val32.p, P.G32.p, v, z, s);
+}
+void tile_sweep_c128(const TilePlan &P, const double2 *v, double2 *z, cudaStream_t s) {
+    OM_REQUIRE(P.ntiles == 0 || P.val64.p != nullptr, "complex128 sweep data was not built for this factor");
+    launch_tile<double2, 8192>(P, P.val64.p, P.G64.p, v, z, s);
+}
+
+void precond_apply(const om_ilu &M, bool conj_transpose, bool fp64, const double2 *v, double2 *z, float2 *tmp32,
+                   cudaStream_t s) {
+    OM_REQUIRE(!conj_transpose || M.has_transpose, "factor built without conjugate transposes");
+    const TilePlan &first = conj_transpose ? M.UH : M.L;
+    const TilePlan &second = conj_transpose ? M.LH : M.U;
+    if (fp64) {
+        OM_REQUIRE(M.has_fp64, "factor built without complex128 sweep data");
+        tile_sweep_c128(first, v, z, s);
+        tile_sweep_c128(second, z, z, s);
+        return;
+    }
+    to_c64(v, M.N, tmp32, s);
+    tile_sweep_c64(first, tmp32, tmp32, s);
+    tile_sweep_c64(second, tmp32, tmp32, s);
+    to_c128(tmp32, M.N, z, s);
+}
+
+}  // namespace omss
+
+void TilePlan::release(cudaStream_t s) {
+    tile_ptr.release(s);
+    col.release(s);
+    val32.release(s);
+    val64.release(s);
+    G32.release(s);
+    G64.release(s);
+    ntiles = 0;
+}

@@ -106,7 +106,7 @@ def test_ilu_apply_matches_oracle(Nc, Nm, d, fill):
     p = SystemParams(Nc, Nm, **BASE)
     A = api.build_liouvillian(p)
     Ar, perm = api.permute(A)
-    M = api.ilu_factor(Ar, d, fill, adjoint=True)
+    M = api.ilu_factor(Ar, d, fill, adjoint=True, fp64_sweeps=True)
     B = gpu_csr(Ar)
     F = ilut(B, d, fill)
     assert M.nnz_l == F.nnz_l and M.nnz_u == F.nnz_u
@@ -127,7 +127,7 @@ def test_complete_lu_solves_exactly():
     p = SystemParams(3, 5, **BASE)
     A = api.build_liouvillian(p)
     Ar, perm = api.permute(A)
-    M = api.ilu_factor(Ar, 0.0, 1e6)
+    M = api.ilu_factor(Ar, 0.0, 1e6, fp64_sweeps=True)
     rng = np.random.default_rng(3)
     x = torch.from_numpy(rng.standard_normal(Ar.N) + 1j * rng.standard_normal(Ar.N)).cuda()
     z = api.ilu_apply(M, api.spmv(Ar, x), fp64=True)
@@ -149,7 +149,7 @@ def test_tiny_solve_matches_dense_lu(mode, precond_fp64):
     w = TINY
     A = api.build_liouvillian(w.params, mode)
     Ar, perm = api.permute(A)
-    M = api.ilu_factor(Ar, w.droptol, w.fill)
+    M = api.ilu_factor(Ar, w.droptol, w.fill, fp64_sweeps=precond_fp64)
     rho, info = api.steady_state_solve(Ar, M, perm, restart=w.restart, tol=w.tol, precond_fp64=precond_fp64)
     rho = rho.cpu().numpy()
     ref = steady_state_dense(oparams(w.params), mode).rho

@@ -34,7 +34,7 @@ def test_noalloc_matches_ilu_apply(Nc, Nm, d, fill):
     p = SystemParams(Nc, Nm, **BASE)
     A = api.build_liouvillian(p)
     Ar, perm = api.permute(A)
-    M = api.ilu_factor(Ar, d, fill, adjoint=True)
+    M = api.ilu_factor(Ar, d, fill, adjoint=True, fp64_sweeps=True)
     rng = np.random.default_rng(11)
     for flags in (0, 1, 2, 3):  # complex64 / complex128 sweeps, plain / conjugate transpose
         ref = torch.empty(Ar.N, dtype=torch.complex128, device="cuda")
