@@ -175,8 +175,8 @@ def steady_state_solve(A_rcm: Matrix, M: ILU, perm: torch.Tensor, restart: int =
 
 
 def steady_state_adjoint(A_rcm: Matrix, M: ILU, perm: torch.Tensor, rho: torch.Tensor, grad_rho: torch.Tensor,
-                         restart: int = 30, max_iters: int = 5000, tol: float = 1e-10, wait_timeout_ns: int = 0,
-                         stream=None):
+                         restart: int = 30, max_iters: int = 5000, tol: float = 1e-12, wait_timeout_ns: int = 0,
+                         precond_fp64: bool = False, stream=None):
     """dF/d(Delta, E, g0, kappa) for a real loss with grad_rho = dF/dRe(rho) + i dF/dIm(rho)."""
     lib = _lib.load()
     n = A_rcm.params.Nc * A_rcm.params.Nm
@@ -184,7 +184,7 @@ def steady_state_adjoint(A_rcm: Matrix, M: ILU, perm: torch.Tensor, rho: torch.T
     g_flat = grad_rho.t().contiguous().view(-1) if grad_rho.dim() == 2 else grad_rho.contiguous()
     _require_cuda(rho_flat, torch.complex128, n * n, "rho")
     _require_cuda(g_flat, torch.complex128, n * n, "grad_rho")
-    o = _opts(restart, max_iters, tol, 0, wait_timeout_ns)
+    o = _opts(restart, max_iters, tol, 0, wait_timeout_ns, precond_fp64)
     p = to_om_params(A_rcm.params)
     out = (ctypes.c_double * 4)()
     info = om_solve_info()
@@ -239,3 +239,45 @@ def profile_read(category: int):
     ms, n = ctypes.c_double(), ctypes.c_int64()
     check(_lib.load().om_profile_read(int(category), ctypes.byref(ms), ctypes.byref(n)), "om_profile_read")
     return ms.value, n.value
+
+
+THETA_NAMES = ("Delta", "E", "g0", "kappa")
+
+
+class SteadyState(torch.autograd.Function):
+    """rho_ss as a differentiable function of theta = (Delta, E, g0, kappa).
+
+    forward(theta, base, options) builds, permutes and factors the
+    Liouvillian at `base` with theta substituted, and returns rho (n x n,
+    complex128, CUDA).  backward solves the adjoint equation
+    L~^H mu = dF/drho with the same permuted ILU and returns
+    dF/dtheta = -Re(mu^H dL~/dtheta rho) (om_steady_state_adjoint)."""
+
+    @staticmethod
+    def forward(ctx, theta, base: SystemParams, options: dict):
+        vals = [float(v) for v in theta.detach().cpu().tolist()]
+        p = base.with_(**dict(zip(THETA_NAMES, vals)))
+        o = dict(options)
+        A = build_liouvillian(p, o.get("trace_mode", "replace"), o.get("nth_floor", 1e-15))
+        Ar, perm = permute(A)
+        A.free()
+        M = ilu_factor(Ar, o.get("droptol", 1e-4), o.get("fill", 10.0), adjoint=True)
+        rho, info = steady_state_solve(Ar, M, perm, restart=o.get("restart", 30), tol=o.get("tol", 1e-12),
+                                       max_iters=o.get("max_iters", 5000))
+        rho = rho.contiguous()
+        ctx.state = (Ar, M, perm, rho, o)
+        ctx.theta_device = theta.device
+        ctx.info = info
+        return rho
+
+    @staticmethod
+    def backward(ctx, grad_rho):
+        Ar, M, perm, rho, o = ctx.state
+        g, _ = steady_state_adjoint(Ar, M, perm, rho, grad_rho.to(torch.complex128), restart=o.get("restart", 30),
+                                    tol=o.get("adjoint_tol", 1e-12), max_iters=o.get("max_iters", 5000))
+        return torch.tensor(g, dtype=torch.float64, device=ctx.theta_device), None, None
+
+
+def steady_state(theta: torch.Tensor, base: SystemParams, **options) -> torch.Tensor:
+    """Differentiable steady state: theta = (Delta, E, g0, kappa) (float64)."""
+    return SteadyState.apply(theta, base, options)

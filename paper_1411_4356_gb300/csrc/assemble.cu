@@ -141,6 +141,10 @@ om_matrix::~om_matrix() {
     d_row0_col.release(s);
     d_row0_val.release(s);
     diag_pos.release(s);
+    val32.release(s);
+    h_rowptr.release(s);
+    h_col.release(s);
+    h_val.release(s);
 }
 
 extern "C" om_status om_build_liouvillian(const om_params *params, const om_build_opts *opts,

@@ -146,6 +146,12 @@ struct om_matrix {
     omss::DBuf<double2> d_row0_val;
     // positions of the diagonal elements rho_ii in this matrix's numbering
     omss::DBuf<int32_t> diag_pos;
+    // built on first use: complex64 copy of the values (mixed precision) and
+    // the conjugate transpose A^H (adjoint)
+    mutable omss::DBuf<float2> val32;
+    mutable omss::DBuf<int64_t> h_rowptr;
+    mutable omss::DBuf<int32_t> h_col;
+    mutable omss::DBuf<double2> h_val;
     cudaStream_t owner_stream = nullptr;
     ~om_matrix();
 };

@@ -8,6 +8,12 @@
 // block order by one block).  The (m+1) x m Hessenberg matrix, its Givens
 // rotations and the residual estimate |g_{j+1}| live in device memory and
 // are updated by a single-thread kernel in FP64.
+//
+// The vectors are complex128 or complex64.  With complex64 vectors each
+// thread accumulates its share of a dot product in FP32 (a few hundred
+// terms) and the partial sums are combined in FP64: GB300 executes FP64 at
+// about 1/64 of the FP32 rate, so FP64 arithmetic per element would make
+// these bandwidth-bound kernels ALU-bound.
 #include <cmath>
 
 #include "krylov.cuh"
@@ -24,6 +30,41 @@ int reduce_blocks(int64_t N) {
     return (int)std::max<int64_t>(1, std::min(need, cap));
 }
 
+unsigned grid_for(int64_t N) {
+    int64_t need = (N + kThreads - 1) / kThreads;
+    int64_t cap = (int64_t)num_sms() * 4;
+    return (unsigned)std::max<int64_t>(1, std::min(need, cap));
+}
+
+// per-thread accumulator type: FP64 for complex128 vectors, FP32 for complex64
+template <class T>
+struct Acc;
+template <>
+struct Acc<double2> {
+    using A = double2;
+    using S = double;
+};
+template <>
+struct Acc<float2> {
+    using A = float2;
+    using S = float;
+};
+
+template <class T>
+__device__ inline T narrow_to(double2 v);
+template <>
+__device__ inline double2 narrow_to<double2>(double2 v) { return v; }
+template <>
+__device__ inline float2 narrow_to<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
+
+template <class T>
+__device__ inline T czero() {
+    T z;
+    z.x = 0;
+    z.y = 0;
+    return z;
+}
+
 __device__ inline double2 warp_sum(double2 v) {
     for (int o = 16; o; o >>= 1) {
         v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
@@ -33,27 +74,29 @@ __device__ inline double2 warp_sum(double2 v) {
 }
 
 // partial[block * ld + first + k] = sum over this block's elements of conj(V_{first+k}) w
-__global__ void __launch_bounds__(kThreads) multidot(const double2 *__restrict__ V, int64_t N, int first, int count,
-                                                     const double2 *__restrict__ w, double2 *partial, int ld) {
+template <class T>
+__global__ void __launch_bounds__(kThreads) multidot(const T *__restrict__ V, int64_t N, int first, int count,
+                                                     const T *__restrict__ w, double2 *partial, int ld) {
+    using A = typename Acc<T>::A;
     __shared__ double2 red[kThreads / 32][kChunk];
-    double2 acc[kChunk];
+    A acc[kChunk];
 #pragma unroll
-    for (int k = 0; k < kChunk; ++k) acc[k] = make_double2(0, 0);
+    for (int k = 0; k < kChunk; ++k) acc[k] = czero<A>();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-        const double2 wi = w[i];
+        const T wi = w[i];
 #pragma unroll
         for (int k = 0; k < kChunk; ++k)
             if (k < count) {
-                const double2 vk = __ldcs(V + (int64_t)(first + k) * N + i);
-                acc[k].x = __fma_rn(vk.x, wi.x, __fma_rn(vk.y, wi.y, acc[k].x));
-                acc[k].y = __fma_rn(vk.x, wi.y, __fma_rn(-vk.y, wi.x, acc[k].y));
+                const T vk = __ldcs(V + (int64_t)(first + k) * N + i);
+                acc[k].x += vk.x * wi.x + vk.y * wi.y;
+                acc[k].y += vk.x * wi.y - vk.y * wi.x;
             }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < kChunk; ++k) {
-        double2 s = warp_sum(acc[k]);
+        double2 s = warp_sum(make_double2((double)acc[k].x, (double)acc[k].y));
         if (lane == 0) red[warp][k] = s;
     }
     __syncthreads();
@@ -74,28 +117,31 @@ __global__ void finish_dots(const double2 *partial, int nblocks, int count, int 
 }
 
 // w -= sum_{k < count} h[k] V_k ; optionally partial sums of |w|^2 per block
-__global__ void __launch_bounds__(kThreads) multi_axpy(const double2 *__restrict__ V, int64_t N, int count,
-                                                       const double2 *__restrict__ h, double2 *w, double *norm_partial) {
-    __shared__ double2 hs[128];
+template <class T>
+__global__ void __launch_bounds__(kThreads) multi_axpy(const T *__restrict__ V, int64_t N, int count,
+                                                       const double2 *__restrict__ h, T *w, double *norm_partial) {
+    using S = typename Acc<T>::S;
+    __shared__ T hs[128];
     __shared__ double red[kThreads / 32];
-    for (int k = threadIdx.x; k < count; k += blockDim.x) hs[k] = h[k];
+    for (int k = threadIdx.x; k < count; k += blockDim.x) hs[k] = narrow_to<T>(h[k]);
     __syncthreads();
-    double nrm = 0;
+    S nrm = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-        double2 wi = w[i];
+        T wi = w[i];
         for (int k = 0; k < count; ++k) {
-            const double2 vk = __ldcs(V + (int64_t)k * N + i);
-            const double2 hk = hs[k];
-            wi.x = __fma_rn(-hk.x, vk.x, __fma_rn(hk.y, vk.y, wi.x));
-            wi.y = __fma_rn(-hk.x, vk.y, __fma_rn(-hk.y, vk.x, wi.y));
+            const T vk = __ldcs(V + (int64_t)k * N + i);
+            const T hk = hs[k];
+            wi.x -= hk.x * vk.x - hk.y * vk.y;
+            wi.y -= hk.x * vk.y + hk.y * vk.x;
         }
         w[i] = wi;
         nrm += wi.x * wi.x + wi.y * wi.y;
     }
     if (norm_partial) {
-        for (int o = 16; o; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+        double d = (double)nrm;
+        for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
         __syncthreads();
         if (threadIdx.x == 0) {
             double s = 0;
@@ -105,25 +151,28 @@ __global__ void __launch_bounds__(kThreads) multi_axpy(const double2 *__restrict
     }
 }
 
-// sum / max partials of a vector (norm^2 and max |x|)
-__global__ void __launch_bounds__(kThreads) vec_stats(const double2 *__restrict__ x, int64_t N, double *part_sum,
+// sum / max partials of |x_i|^2
+template <class T>
+__global__ void __launch_bounds__(kThreads) vec_stats(const T *__restrict__ x, int64_t N, double *part_sum,
                                                       double *part_max) {
+    using S = typename Acc<T>::S;
     __shared__ double rs[kThreads / 32], rm[kThreads / 32];
-    double s = 0, m = 0;
+    S s = 0, m = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-        double2 v = x[i];
-        double a = v.x * v.x + v.y * v.y;
+        T v = x[i];
+        S a = v.x * v.x + v.y * v.y;
         s += a;
-        m = fmax(m, a);
+        m = a > m ? a : m;
     }
+    double ds = (double)s, dm = (double)m;
     for (int o = 16; o; o >>= 1) {
-        s += __shfl_xor_sync(0xffffffffu, s, o);
-        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        ds += __shfl_xor_sync(0xffffffffu, ds, o);
+        dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
     }
     if ((threadIdx.x & 31) == 0) {
-        rs[threadIdx.x >> 5] = s;
-        rm[threadIdx.x >> 5] = m;
+        rs[threadIdx.x >> 5] = ds;
+        rm[threadIdx.x >> 5] = dm;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -156,10 +205,29 @@ __global__ void finish_norm(const double *ps, int nblocks, double *out) {
     out[0] = sqrt(s);
 }
 
-__global__ void scale_into(const double2 *__restrict__ w, const double *nrm, int64_t N, double2 *__restrict__ v) {
+template <class T>
+__global__ void scale_into(const T *__restrict__ w, const double *nrm, int64_t N, T *__restrict__ v) {
     const double inv = nrm[0] > 0 ? 1.0 / nrm[0] : 0.0;
+    const typename Acc<T>::S sc = (typename Acc<T>::S)inv;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) v[i] = cscale(w[i], inv);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        T a = w[i];
+        a.x *= sc;
+        a.y *= sc;
+        v[i] = a;
+    }
+}
+
+// y = b - y  (residual r = b - A x with A x already in y)
+template <class T>
+__global__ void rsub(const T *__restrict__ b, T *y, int64_t N) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        T a = y[i], c = b[i];
+        a.x = c.x - a.x;
+        a.y = c.y - a.y;
+        y[i] = a;
+    }
 }
 
 __global__ void axpby_kernel(double2 a, const double2 *__restrict__ x, double2 b, double2 *y, int64_t N) {
@@ -168,17 +236,21 @@ __global__ void axpby_kernel(double2 a, const double2 *__restrict__ x, double2 b
         y[i] = cadd(cmul(a, x[i]), cmul(b, y[i]));
 }
 
-// u = sum_{k < count} y[k] V_k
-__global__ void combine(const double2 *__restrict__ V, int64_t N, int count, const double2 *__restrict__ y,
-                        double2 *__restrict__ u) {
-    __shared__ double2 ys[128];
-    for (int k = threadIdx.x; k < count; k += blockDim.x) ys[k] = y[k];
+// x += sum_{k < count} y[k] Z_k
+template <class T>
+__global__ void combine_add(const T *__restrict__ Z, int64_t N, int count, const double2 *__restrict__ y, T *x) {
+    __shared__ T ys[128];
+    for (int k = threadIdx.x; k < count; k += blockDim.x) ys[k] = narrow_to<T>(y[k]);
     __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-        double2 s = make_double2(0, 0);
-        for (int k = 0; k < count; ++k) s = cadd(s, cmul(ys[k], __ldcs(V + (int64_t)k * N + i)));
-        u[i] = s;
+        T s = x[i];
+        for (int k = 0; k < count; ++k) {
+            const T zk = __ldcs(Z + (int64_t)k * N + i);
+            s.x += ys[k].x * zk.x - ys[k].y * zk.y;
+            s.y += ys[k].x * zk.y + ys[k].y * zk.x;
+        }
+        x[i] = s;
     }
 }
 
@@ -243,17 +315,18 @@ __global__ void init_g(double2 *g, int m1, const double *beta) {
 
 }  // namespace
 
-void GmresWork::alloc(int64_t n_, int m_, cudaStream_t s) {
+template <class T>
+void GmresWork<T>::alloc(int64_t n_, int m_, cudaStream_t s) {
     N = n_;
     m = m_;
     V.alloc((size_t)(m + 1) * N, s);
     Z.alloc((size_t)m * N, s);
-    tmp32.alloc(N, s);
     w.alloc(N, s);
-    z.alloc(N, s);
     r.alloc(N, s);
+    tmp32.alloc(N, s);
     partial.alloc((size_t)reduce_blocks(N) * (m + 2), s);
     h.alloc(m + 2, s);
+    y2.alloc(m + 2, s);
     H.alloc((size_t)(m + 1) * m, s);
     cs.alloc(m + 1, s);
     sn.alloc(m + 1, s);
@@ -262,15 +335,16 @@ void GmresWork::alloc(int64_t n_, int m_, cudaStream_t s) {
     scal.alloc(4 * 1024 + 8, s);
 }
 
-void GmresWork::release(cudaStream_t s) {
+template <class T>
+void GmresWork<T>::release(cudaStream_t s) {
     V.release(s);
     Z.release(s);
-    tmp32.release(s);
     w.release(s);
-    z.release(s);
     r.release(s);
+    tmp32.release(s);
     partial.release(s);
     h.release(s);
+    y2.release(s);
     H.release(s);
     cs.release(s);
     sn.release(s);
@@ -279,14 +353,9 @@ void GmresWork::release(cudaStream_t s) {
     scal.release(s);
 }
 
-static unsigned grid_for(int64_t N) {
-    int64_t need = (N + kThreads - 1) / kThreads;
-    int64_t cap = (int64_t)num_sms() * 4;
-    return (unsigned)std::max<int64_t>(1, std::min(need, cap));
-}
-
 void dev_axpby(double2 a, const double2 *x, double2 b, double2 *y, int64_t N, cudaStream_t s) {
-    axpby_kernel<<<grid_for(N), kThreads, 0, s>>>(a, x, b, y, N); omss::note_launch();
+    axpby_kernel<<<grid_for(N), kThreads, 0, s>>>(a, x, b, y, N);
+    omss::note_launch();
     OM_CHECK_LAUNCH();
 }
 void dev_copy(const double2 *x, double2 *y, int64_t N, cudaStream_t s) {
@@ -296,30 +365,27 @@ void dev_zero(double2 *x, int64_t N, cudaStream_t s) {
     OM_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double2) * N, s));
 }
 
-// scal layout: [0] est, [1] norm, [2] stats sum, [3] stats max, [8 ...] partial sums, [8+1024 ...] partial maxes
-static void stats(const double2 *x, int64_t N, GmresWork &W, cudaStream_t s, double *out2) {
+// scal layout: [0] est, [1] norm, [2] stats norm, [3] stats max, [4..7] scratch,
+// [8 ...] partial sums (<= 2048), [8 + 2048 ...] partial maxes
+template <class T>
+void dev_stats(const T *x, int64_t N, GmresWork<T> &W, cudaStream_t s, double *norm2, double *maxabs) {
     int nb = reduce_blocks(N);
     double *ps = W.scal.p + 8, *pm = W.scal.p + 8 + 2048;
-    vec_stats<<<nb, kThreads, 0, s>>>(x, N, ps, pm); omss::note_launch();
-    finish_stats<<<1, 32, 0, s>>>(ps, pm, nb, W.scal.p + 2); omss::note_launch();
+    vec_stats<T><<<nb, kThreads, 0, s>>>(x, N, ps, pm);
+    omss::note_launch();
+    finish_stats<<<1, 32, 0, s>>>(ps, pm, nb, W.scal.p + 2);
+    omss::note_launch();
     OM_CHECK_LAUNCH();
-    OM_CUDA_TRY(cudaMemcpyAsync(out2, W.scal.p + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    double o[2];
+    OM_CUDA_TRY(cudaMemcpyAsync(o, W.scal.p + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     OM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (norm2) *norm2 = o[0];
+    if (maxabs) *maxabs = o[1];
 }
 
-double dev_norm2(const double2 *x, int64_t N, GmresWork &W, cudaStream_t s) {
-    double o[2];
-    stats(x, N, W, s, o);
-    return o[0];
-}
-double dev_maxabs(const double2 *x, int64_t N, GmresWork &W, cudaStream_t s) {
-    double o[2];
-    stats(x, N, W, s, o);
-    return o[1];
-}
-
-GmresResult gmres_cycle(KrylovOps &ops, const double2 *b, double2 *x, double target, int max_iters,
-                        GmresWork &W, cudaStream_t s) {
+template <class T>
+GmresResult gmres_cycle(KrylovOps<T> &ops, const T *b, T *x, double target, int max_iters, GmresWork<T> &W,
+                        cudaStream_t s) {
     GmresResult res;
     const int64_t N = W.N;
     const int m = W.m;
@@ -329,45 +395,57 @@ GmresResult gmres_cycle(KrylovOps &ops, const double2 *b, double2 *x, double tar
     double *d_nrm = W.scal.p + 1;
     // r = b - A x
     ops.apply(x, W.r.p, s);
-    dev_axpby(make_double2(1, 0), b, make_double2(-1, 0), W.r.p, N, s);
-    double beta = dev_norm2(W.r.p, N, W, s);
+    rsub<T><<<grid_for(N), kThreads, 0, s>>>(b, W.r.p, N);
+    omss::note_launch();
+    OM_CHECK_LAUNCH();
+    double beta = 0;
+    dev_stats<T>(W.r.p, N, W, s, &beta, nullptr);
+    res.beta = beta;
     res.last_estimate = beta;
     if (!(beta > 0) || !std::isfinite(beta)) {
         res.breakdown = !std::isfinite(beta);
         return res;
     }
     OM_CUDA_TRY(cudaMemcpyAsync(d_nrm, W.scal.p + 2, sizeof(double), cudaMemcpyDeviceToDevice, s));
-    scale_into<<<grid_for(N), kThreads, 0, s>>>(W.r.p, d_nrm, N, W.V.p); omss::note_launch();
-    init_g<<<1, 128, 0, s>>>(W.g.p, m + 2, d_nrm); omss::note_launch();
+    scale_into<T><<<grid_for(N), kThreads, 0, s>>>(W.r.p, d_nrm, N, W.V.p);
+    omss::note_launch();
+    init_g<<<1, 128, 0, s>>>(W.g.p, m + 2, d_nrm);
+    omss::note_launch();
     OM_CHECK_LAUNCH();
     int k = 0;
     double est = beta;
     for (int j = 0; j < m && res.iterations < max_iters; ++j) {
-        double2 *vj = W.V.p + (int64_t)j * N;
-        double2 *vnext = W.V.p + (int64_t)(j + 1) * N;
-        double2 *zj = W.Z.p + (int64_t)j * N;
+        T *vj = W.V.p + (int64_t)j * N;
+        T *vnext = W.V.p + (int64_t)(j + 1) * N;
+        T *zj = W.Z.p + (int64_t)j * N;
         ops.precond(vj, zj, s);
         ops.apply(zj, W.w.p, s);
-        // CGS2
+        // CGS2: h1 = V^H w, w -= V h1; h2 = V^H w, w -= V h2; h = h1 + h2
         for (int pass = 0; pass < 2; ++pass) {
             for (int f = 0; f <= j; f += kChunk) {
                 int cnt = std::min(kChunk, j + 1 - f);
-                multidot<<<nb, kThreads, 0, s>>>(W.V.p, N, f, cnt, W.w.p, W.partial.p, ld); omss::note_launch();
+                multidot<T><<<nb, kThreads, 0, s>>>(W.V.p, N, f, cnt, W.w.p, W.partial.p, ld);
+                omss::note_launch();
             }
-            finish_dots<<<1, 128, 0, s>>>(W.partial.p, nb, j + 1, ld, W.h.p, pass); omss::note_launch();
-            // second pass corrects with the re-orthogonalisation coefficients only
+            finish_dots<<<1, 128, 0, s>>>(W.partial.p, nb, j + 1, ld, W.h.p, pass);
+            omss::note_launch();
             if (pass == 0) {
-                multi_axpy<<<nb, kThreads, 0, s>>>(W.V.p, N, j + 1, W.h.p, W.w.p, nullptr); omss::note_launch();
+                multi_axpy<T><<<nb, kThreads, 0, s>>>(W.V.p, N, j + 1, W.h.p, W.w.p, nullptr);
+                omss::note_launch();
             } else {
-                // h holds h1 + h2; the update uses h2 = partial sums just computed
-                finish_dots<<<1, 128, 0, s>>>(W.partial.p, nb, j + 1, ld, W.y.p, 0); omss::note_launch();
-                multi_axpy<<<nb, kThreads, 0, s>>>(W.V.p, N, j + 1, W.y.p, W.w.p, W.scal.p + 8); omss::note_launch();
-                finish_norm<<<1, 32, 0, s>>>(W.scal.p + 8, nb, d_nrm); omss::note_launch();
+                finish_dots<<<1, 128, 0, s>>>(W.partial.p, nb, j + 1, ld, W.y2.p, 0);
+                omss::note_launch();
+                multi_axpy<T><<<nb, kThreads, 0, s>>>(W.V.p, N, j + 1, W.y2.p, W.w.p, W.scal.p + 8);
+                omss::note_launch();
+                finish_norm<<<1, 32, 0, s>>>(W.scal.p + 8, nb, d_nrm);
+                omss::note_launch();
             }
             OM_CHECK_LAUNCH();
         }
-        scale_into<<<grid_for(N), kThreads, 0, s>>>(W.w.p, d_nrm, N, vnext); omss::note_launch();
-        givens_step<<<1, 1, 0, s>>>(W.H.p, m + 1, W.cs.p, W.sn.p, W.g.p, W.h.p, d_nrm, j, d_est); omss::note_launch();
+        scale_into<T><<<grid_for(N), kThreads, 0, s>>>(W.w.p, d_nrm, N, vnext);
+        omss::note_launch();
+        givens_step<<<1, 1, 0, s>>>(W.H.p, m + 1, W.cs.p, W.sn.p, W.g.p, W.h.p, d_nrm, j, d_est);
+        omss::note_launch();
         OM_CHECK_LAUNCH();
         double hn[2];
         OM_CUDA_TRY(cudaMemcpyAsync(hn, W.scal.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -383,13 +461,22 @@ GmresResult gmres_cycle(KrylovOps &ops, const double2 *b, double2 *x, double tar
     }
     res.last_estimate = est;
     if (k > 0) {
-        back_substitute<<<1, 1, 0, s>>>(W.H.p, m + 1, W.g.p, k, W.y.p); omss::note_launch();
-        combine<<<grid_for(N), kThreads, 0, s>>>(W.Z.p, N, k, W.y.p, W.w.p); omss::note_launch();
+        back_substitute<<<1, 1, 0, s>>>(W.H.p, m + 1, W.g.p, k, W.y.p);
+        omss::note_launch();
+        combine_add<T><<<grid_for(N), kThreads, 0, s>>>(W.Z.p, N, k, W.y.p, x);
+        omss::note_launch();
         OM_CHECK_LAUNCH();
-        dev_axpby(make_double2(1, 0), W.w.p, make_double2(1, 0), x, N, s);
     }
-    res.cycles = 1;
     return res;
 }
+
+template struct GmresWork<double2>;
+template struct GmresWork<float2>;
+template GmresResult gmres_cycle<double2>(KrylovOps<double2> &, const double2 *, double2 *, double, int,
+                                          GmresWork<double2> &, cudaStream_t);
+template GmresResult gmres_cycle<float2>(KrylovOps<float2> &, const float2 *, float2 *, double, int,
+                                         GmresWork<float2> &, cudaStream_t);
+template void dev_stats<double2>(const double2 *, int64_t, GmresWork<double2> &, cudaStream_t, double *, double *);
+template void dev_stats<float2>(const float2 *, int64_t, GmresWork<float2> &, cudaStream_t, double *, double *);
 
 }  // namespace omss

@@ -77,7 +77,7 @@ __global__ void observables_kernel(int Nc, int Nm, const double2 *rho, double *o
     }
 }
 
-struct ForwardOps : KrylovOps {
+struct ForwardOps : KrylovOps<double2> {
     const om_matrix *A;
     const om_ilu *M;
     bool fp64_precond;
@@ -93,16 +93,17 @@ struct ForwardOps : KrylovOps {
 }  // namespace
 
 // eta of x for the unmodified Liouvillian; y is scratch of length N
-double eta_of(const om_matrix &A, const double2 *x, double2 *y, GmresWork &W, cudaStream_t s) {
+double eta_of(const om_matrix &A, const double2 *x, double2 *y, GmresWork<double2> &W, cudaStream_t s) {
     spmv_c128(A.rowptr.p, A.col.p, A.val.p, A.N, x, y, s);
     fix_trace_row<<<1, 1, 0, s>>>(y, x, A.trace_row, A.d_row0_col.p, A.d_row0_val.p, (int)A.row0_col.size()); omss::note_launch();
     OM_CHECK_LAUNCH();
-    double ly = dev_maxabs(y, A.N, W, s);
-    double lx = dev_maxabs(x, A.N, W, s);
+    double ly = 0, lx = 0;
+    dev_stats<double2>(y, A.N, W, s, nullptr, &ly);
+    dev_stats<double2>(x, A.N, W, s, nullptr, &lx);
     return ly / (A.norm_inf * lx);
 }
 
-double2 trace_of(const om_matrix &A, const double2 *x, GmresWork &W, cudaStream_t s) {
+double2 trace_of(const om_matrix &A, const double2 *x, GmresWork<double2> &W, cudaStream_t s) {
     double2 *t = reinterpret_cast<double2 *>(W.scal.p + 4);
     gather_sum<<<1, 256, 0, s>>>(x, A.diag_pos.p, A.n, t); omss::note_launch();
     OM_CHECK_LAUNCH();
@@ -112,8 +113,8 @@ double2 trace_of(const om_matrix &A, const double2 *x, GmresWork &W, cudaStream_
     return h;
 }
 
-void normalise_into_rho(const om_matrix &A, const double2 *x, const int32_t *perm, double2 *rho, GmresWork &W,
-                        cudaStream_t s) {
+void normalise_into_rho(const om_matrix &A, const double2 *x, const int32_t *perm, double2 *rho,
+                        GmresWork<double2> &W, cudaStream_t s) {
     double2 *t = reinterpret_cast<double2 *>(W.scal.p + 4);
     gather_sum<<<1, 256, 0, s>>>(x, A.diag_pos.p, A.n, t); omss::note_launch();
     int64_t need = (A.N + 255) / 256;
@@ -126,7 +127,9 @@ void normalise_into_rho(const om_matrix &A, const double2 *x, const int32_t *per
 
 using namespace omss;
 
-static void check_solve_args(const om_matrix *A, const om_ilu *M, const int32_t *perm, const om_solve_opts *o) {
+
+namespace omss {
+void check_solve_args(const om_matrix *A, const om_ilu *M, const int32_t *perm, const om_solve_opts *o) {
     OM_REQUIRE(A && M && perm && o, "NULL argument");
     OM_REQUIRE(A->permuted, "the matrix must come from om_permute");
     OM_REQUIRE(M->N == A->N, "ILU and matrix sizes differ");
@@ -135,8 +138,6 @@ static void check_solve_args(const om_matrix *A, const om_ilu *M, const int32_t 
     OM_REQUIRE(o->tol > 0, "tol must be positive");
     OM_REQUIRE(o->precision == 0 || o->precision == 1, "precision must be 0 or 1");
 }
-
-namespace omss {
 om_status solve_mixed(const om_matrix *A, const om_ilu *M, const int32_t *perm_dev, const om_solve_opts *opts,
                       const double *x0, double *rho_dev, om_solve_info *info, void *stream);
 }
@@ -152,7 +153,7 @@ extern "C" om_status om_steady_state_solve(const om_matrix *A, const om_ilu *M, 
         auto t0 = std::chrono::steady_clock::now();
         cudaStream_t s = as_stream(stream);
         const int64_t N = A->N;
-        GmresWork W;
+        GmresWork<double2> W;
         W.alloc(N, opts->restart, s);
         DBuf<double2> b, x;
         b.alloc(N, s);
@@ -177,7 +178,7 @@ extern "C" om_status om_steady_state_solve(const om_matrix *A, const om_ilu *M, 
             its += r.iterations;
             ++cycles;
             eta = eta_of(*A, x.p, W.w.p, W, s);
-            xinf = dev_maxabs(x.p, N, W, s);
+            dev_stats<double2>(x.p, N, W, s, nullptr, &xinf);
             if (cycles <= 64) inf.residual_history[cycles - 1] = eta;
             if (!std::isfinite(eta)) {
                 final_status = OM_ENUMERIC;

@@ -1,0 +1,97 @@
+"""Mixed precision (complex64 inner solves inside FP64 refinement) and the
+adjoint gradients, through the C ABI, against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle.liouvillian import Params
+from oracle.steady import adjoint_gradient_dense, observable_vec, steady_state_dense, steady_state_iterative
+from paper_1411_4356_gb300 import api
+from paper_1411_4356_gb300.workloads import SystemParams
+
+pytestmark = pytest.mark.gpu
+
+BASE = dict(omega_m=1.0, Delta=-1.0, kappa=0.5, g0=0.3, E=0.2, Q_m=1e3, n_th=0.5)
+
+
+def oparams(p):
+    return Params(p.Nc, p.Nm, p.omega_m, p.Delta, p.kappa, p.g0, p.E, p.Q_m, p.n_th)
+
+
+def factor(p, d, fill, mode="replace", adjoint=False):
+    A = api.build_liouvillian(p, mode)
+    Ar, perm = api.permute(A)
+    M = api.ilu_factor(Ar, d, fill, adjoint=adjoint)
+    return Ar, perm, M
+
+
+@pytest.mark.parametrize("Nc,Nm,d,fill", [(4, 10, 1e-4, 10.0), (4, 8, 1e-4, 10.0)])
+def test_mixed_matches_dense(Nc, Nm, d, fill):
+    p = SystemParams(Nc, Nm, **BASE)
+    Ar, perm, M = factor(p, d, fill)
+    rho, info = api.steady_state_solve(Ar, M, perm, restart=30, tol=1e-12, precision=1)
+    ref = steady_state_dense(oparams(p)).rho
+    assert info.eta <= 1e-12
+    assert np.abs(rho.cpu().numpy() - ref).max() <= 1e-9
+
+
+def test_mixed_matches_fp64_path_and_oracle_at_14400_rows():
+    """eta bounds the backward error only.  Errors along the slowly decaying
+    mechanical modes (rate ~Gamma_m) barely move L rho, so at eta = 1e-12 the
+    forward error can still be ~1e-9; both precisions solve to 1e-13 here."""
+    p = SystemParams(6, 20, 1.0, -1.3, 0.4, 0.8, 0.2, 1e3, 0.2)
+    Ar, perm, M = factor(p, 1e-4, 20.0)
+    r64, i64 = api.steady_state_solve(Ar, M, perm, restart=30, tol=1e-13, precision=0)
+    r32, i32 = api.steady_state_solve(Ar, M, perm, restart=30, tol=1e-13, precision=1)
+    ref = steady_state_iterative(oparams(p), droptol=1e-4, fill=20.0, restart=50, rtol=1e-15)
+    print("eta", i64.eta, i32.eta, "err64", np.abs(r64.cpu().numpy() - ref.rho).max(),
+          "err32", np.abs(r32.cpu().numpy() - ref.rho).max(), "its", i64.iterations, i32.iterations, i32.cycles)
+    assert i64.eta <= 1e-13 and i32.eta <= 1e-13
+    assert np.abs(r32.cpu().numpy() - ref.rho).max() <= 1e-9
+    assert np.abs(r64.cpu().numpy() - ref.rho).max() <= 1e-9
+
+
+@pytest.mark.parametrize("mode", ["replace", "add"])
+@pytest.mark.parametrize("which", ["n_a", "n_b"])
+def test_adjoint_matches_oracle(mode, which):
+    """The oracle's adjoint is itself pinned to central differences."""
+    p = SystemParams(4, 10, **BASE)
+    Ar, perm, M = factor(p, 1e-4, 10.0, mode, adjoint=True)
+    rho, info = api.steady_state_solve(Ar, M, perm, restart=30, tol=1e-13)
+    G = observable_vec(oparams(p), which)
+    n = p.Nc * p.Nm
+    G_t = torch.from_numpy(G.reshape((n, n), order="F")).cuda()
+    g, ainfo = api.steady_state_adjoint(Ar, M, perm, rho, G_t, restart=30, tol=1e-13)
+    ref = adjoint_gradient_dense(oparams(p), G, mode)
+    for t, name in enumerate(("Delta", "E", "g0", "kappa")):
+        assert g[t] == pytest.approx(ref[name], rel=1e-8, abs=1e-12), (name, g[t], ref[name])
+
+
+def test_autograd_function_against_central_differences():
+    """dF/dtheta through torch.autograd (F = <b^dag b>) against central
+    differences of the GPU forward solve itself."""
+    base = SystemParams(3, 8, **BASE)
+    theta0 = [base.Delta, base.E, base.g0, base.kappa]
+    opts = dict(droptol=1e-4, fill=10.0, tol=1e-14, restart=30)
+    n = base.Nc * base.Nm
+    m = torch.tensor([h % base.Nm for h in range(n)], dtype=torch.float64, device="cuda")
+
+    def F(theta):
+        rho = api.steady_state(theta, base, **opts)
+        return (torch.diagonal(rho).real * m).sum()
+
+    theta = torch.tensor(theta0, dtype=torch.float64, requires_grad=True)
+    val = F(theta)
+    val.backward()
+    grad = theta.grad.numpy()
+    def central(t, h):
+        up = torch.tensor(theta0, dtype=torch.float64)
+        dn = torch.tensor(theta0, dtype=torch.float64)
+        up[t] += h
+        dn[t] -= h
+        return (F(up).item() - F(dn).item()) / (2 * h)
+
+    for t in range(4):
+        # Richardson extrapolation of central differences (truncation O(h^4))
+        fd = (4 * central(t, 5e-5) - central(t, 1e-4)) / 3
+        assert grad[t] == pytest.approx(fd, rel=1e-6, abs=1e-9), (t, grad[t], fd)
