@@ -174,6 +174,23 @@ om_status om_steady_state_adjoint(const om_matrix *A_rcm, const om_ilu *M, const
                                   const double *rho_dev, const double *grad_rho_dev,
                                   double grad_out[4], om_solve_info *info, void *stream);
 
+/* ---- batched steady states --------------------------------------------------
+ * Solves `count` independent systems (a parameter sweep, Sec. IV) with
+ * om_steady_state_solve semantics, up to `concurrency` at a time (<= 0:
+ * twice the SM count), each on its own stream driven by its own host thread,
+ * so that the single-block sweeps of different systems run on different
+ * SMs at once.  A_rcm[i], M[i], perm_dev[i], rho_dev[i] are as for
+ * om_steady_state_solve (x0 is not taken); opts applies to all.  status[i]
+ * (HOST, count entries) receives each solve's status and info[i] (HOST, may
+ * be NULL) its statistics.  Inputs written on `stream` before the call are
+ * honoured, and the results are ordered before later work on `stream`.
+ * Returns OM_OK if the batch ran (check status[]), else OM_EINVAL/OM_ECUDA. */
+om_status om_steady_state_solve_batched(int32_t count, const om_matrix *const *A_rcm,
+                                        const om_ilu *const *M, const int32_t *const *perm_dev,
+                                        const om_solve_opts *opts, double *const *rho_dev,
+                                        om_solve_info *info, om_status *status, int32_t concurrency,
+                                        void *stream);
+
 /* ---- single kernels, exposed for parity tests -------------------------------
  * y = A x (DEVICE c128 vectors of length nrows). */
 om_status om_spmv(const om_matrix *A, const double *x, double *y, void *stream);

@@ -281,3 +281,31 @@ class SteadyState(torch.autograd.Function):
 def steady_state(theta: torch.Tensor, base: SystemParams, **options) -> torch.Tensor:
     """Differentiable steady state: theta = (Delta, E, g0, kappa) (float64)."""
     return SteadyState.apply(theta, base, options)
+
+
+def steady_state_solve_batched(systems, restart: int = 30, max_iters: int = 5000, tol: float = 1e-10,
+                               precision: int = 0, concurrency: int = 0, stream=None):
+    """Solve many (A_rcm, M, perm) systems concurrently (om_steady_state_solve_batched).
+
+    Returns ([rho n x n CUDA tensors], [SolveInfo])."""
+    lib = _lib.load()
+    count = len(systems)
+    Ah = (ctypes.c_void_p * count)(*[A.handle.value for A, M, perm in systems])
+    Mh = (ctypes.c_void_p * count)(*[M.handle.value for A, M, perm in systems])
+    Ph = (ctypes.c_void_p * count)(*[perm.data_ptr() for A, M, perm in systems])
+    rhos = [torch.empty(A.params.Nc * A.params.Nm * A.params.Nc * A.params.Nm, dtype=torch.complex128,
+                        device="cuda") for A, M, perm in systems]
+    Rh = (ctypes.c_void_p * count)(*[r.data_ptr() for r in rhos])
+    infos = (om_solve_info * count)()
+    status = (ctypes.c_int32 * count)()
+    o = _opts(restart, max_iters, tol, precision, 0)
+    check(lib.om_steady_state_solve_batched(count, Ah, Mh, Ph, ctypes.byref(o), Rh, infos, status, int(concurrency),
+                                            ctypes.c_void_p(_stream(stream))), "om_steady_state_solve_batched")
+    out_rho, out_info = [], []
+    for i, (A, M, perm) in enumerate(systems):
+        n = A.params.Nc * A.params.Nm
+        out_rho.append(rhos[i].view(n, n).t())
+        inf = infos[i]
+        out_info.append(SolveInfo(inf.iterations, inf.cycles, inf.eta, inf.trace_before, inf.seconds,
+                                  list(inf.residual_history[:min(inf.cycles, 64)]), int(status[i])))
+    return out_rho, out_info
