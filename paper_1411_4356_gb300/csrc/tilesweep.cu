@@ -14,14 +14,17 @@
 //  * Setup stores G_T = D_T^{-1} (dense, computed in FP64 on the host cores)
 //    and E_T in a sliced-ELL layout per tile (slot k of the 32 rows is
 //    contiguous, padded with zero entries).
-//  * One thread block runs the tiles in order.  Phase A: all 16 warps share
-//    the slots of E_T (each a contiguous run, loaded eight slots at a time so
-//    the loads overlap), each lane owning one row, and leave partial sums in
-//    shared memory; earlier x values come from a shared-memory ring of WIN
-//    rows or, when older, from global memory.  Phase B: warp 0 forms
-//    y = v_T - E_T x and x_T = G_T y with 32 warp shuffles, then writes x_T.
-//    A __syncthreads separates the phases; nothing spins.
-//  * The next tiles' data is prefetched into L2 with cp.async.bulk.prefetch.
+//  * One thread block runs the tiles in order.  A producer warp streams the
+//    slots of E_T, in chunks of 32 slots (12 KB in complex64), into a ring of
+//    shared-memory stages with TMA bulk copies (cp.async.bulk, completion on
+//    full/empty mbarriers), so that up to eight chunks are in flight.
+//    Phase A: the 16 compute warps share the slots of each chunk, each lane
+//    owning one row, and leave partial sums in shared memory; earlier x
+//    values come from a shared-memory ring of WIN rows or, when older, from
+//    global memory.  Phase B: warp 0 forms y = v_T - E_T x and x_T = G_T y
+//    with 32 warp shuffles, then writes x_T.  A named barrier of the compute
+//    warps separates the phases.  Every mbarrier wait is bounded (2 s); a
+//    wait that runs out aborts the sweep and its results read as NaN.
 //
 // A tile's 32 rows thus cost one barrier round instead of up to 32 dependent
 // hops; the sweep is bounded by the bandwidth one SM can draw and by the
@@ -60,93 +63,144 @@ struct TOps<float2> {
     __device__ static float2 add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 };
 
-__device__ inline void prefetch_l2(const void *p, uint32_t bytes) {
-    // bulk prefetch of a contiguous range into L2 (16-byte aligned, multiple of 16 bytes)
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+__device__ inline uint32_t smem_u32(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+__device__ inline void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
+__device__ inline void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ inline void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ inline bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// global -> shared bulk copy (TMA, no tensor map) completing on an mbarrier
+__device__ inline void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ inline uint64_t now_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ inline void consumer_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(kTileWarps * 32) : "memory"); }
 
-__device__ inline void prefetch_range(const void *base, size_t elem, int64_t begin, int64_t end) {
-    // align the byte range to 16 bytes and split it into pieces below 1 MiB
-    uintptr_t lo = (reinterpret_cast<uintptr_t>(base) + (uintptr_t)begin * elem) & ~uintptr_t(15);
-    uintptr_t hi = (reinterpret_cast<uintptr_t>(base) + (uintptr_t)end * elem + 15) & ~uintptr_t(15);
-    while (lo < hi) {
-        const uintptr_t rest = hi - lo;
-        const uint32_t n = (uint32_t)(rest < (uintptr_t(1) << 19) ? rest : (uintptr_t(1) << 19));
-        prefetch_l2(reinterpret_cast<const void *>(lo), n);
-        lo += n;
+// Waits for an mbarrier phase; gives up after 2 s or once `abort` is set,
+// setting `abort` so that every other wait of the block returns at once.
+__device__ inline bool wait_phase(uint64_t *bar, uint32_t parity, volatile int *abort) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t start = now_ns();
+    for (;;) {
+        if (*abort) return false;
+        if (mbar_try_wait(bar, parity)) return true;
+        if (now_ns() - start > 2000000000ull) {
+            *abort = 1;
+            return false;
+        }
     }
 }
 
+constexpr int kChunkSlots = 32;  // slots (of 32 rows) per streamed chunk
+
 // v, z: natural-order vectors (index r); the tile data is in sweep order t.
-template <class CT, int WIN>
-__global__ void __launch_bounds__(kTileWarps * 32, 1)
+// Warps 0..15 compute; warp 16 streams the tiles' slots into a ring of
+// STAGES shared-memory buffers with bulk copies (full / empty mbarriers).
+template <class CT, int WIN, int STAGES>
+__global__ void __launch_bounds__((kTileWarps + 1) * 32, 1)
 tile_sweep(int64_t N, int64_t ntiles, int forward, const int64_t *__restrict__ tile_ptr,
            const int32_t *__restrict__ scol, const CT *__restrict__ sval, const CT *__restrict__ G,
            const CT *v, CT *z) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    CT *win = reinterpret_cast<CT *>(smem_raw);                      // WIN rows of x, by t
-    CT *part = win + WIN;                                              // kTileWarps x 32 partial sums
-    CT *gs = part + kTileWarps * kTile;                                // 32 x 32 inverse of the tile
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    int32_t *col_s = reinterpret_cast<int32_t *>(smem_raw);
+    CT *val_s = reinterpret_cast<CT *>(smem_raw + sizeof(int32_t) * STAGES * kChunkSlots * kTile);
+    CT *win = val_s + STAGES * kChunkSlots * kTile;  // WIN rows of x, by t
+    CT *part = win + WIN;                             // kTileWarps x 32 partial sums
+    CT *gs = part + kTileWarps * kTile;               // 32 x 32 inverse of the tile
+    uint64_t *full = reinterpret_cast<uint64_t *>(gs + kTile * kTile);
+    uint64_t *empty = full + STAGES;
+    __shared__ volatile int abort_flag;
     using O = TOps<CT>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
-        for (int64_t q = 0; q < 2 && q < ntiles; ++q)
-            prefetch_range(scol, sizeof(int32_t), tile_ptr[q], tile_ptr[q + 1]),
-                prefetch_range(sval, sizeof(CT), tile_ptr[q], tile_ptr[q + 1]);
+        abort_flag = 0;
+        for (int q = 0; q < STAGES; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], kTileWarps);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    __syncthreads();
+
+    if (warp == kTileWarps) {  // producer
+        if (lane == 0) {
+            int64_t g = 0;
+            for (int64_t T = 0; T < ntiles && !abort_flag; ++T) {
+                const int64_t b = tile_ptr[T];
+                const int64_t width = (tile_ptr[T + 1] - b) / kTile;
+                for (int64_t c = 0; c < width; c += kChunkSlots, ++g) {
+                    const int ns = (int)((width - c) < kChunkSlots ? (width - c) : kChunkSlots);
+                    const int stage = (int)(g % STAGES);
+                    const uint32_t use = (uint32_t)(g / STAGES);
+                    if (g >= STAGES && !wait_phase(&empty[stage], (use - 1) & 1, &abort_flag)) return;
+                    const uint32_t bc = (uint32_t)(ns * kTile * sizeof(int32_t));
+                    const uint32_t bv = (uint32_t)(ns * kTile * sizeof(CT));
+                    mbar_expect_tx(&full[stage], bc + bv);
+                    bulk_g2s(col_s + stage * kChunkSlots * kTile, scol + b + c * kTile, bc, &full[stage]);
+                    bulk_g2s(val_s + stage * kChunkSlots * kTile, sval + b + c * kTile, bv, &full[stage]);
+                }
+            }
+        }
+        return;
+    }
+
+    int64_t g = 0;
     for (int64_t T = 0; T < ntiles; ++T) {
         const int64_t t0 = T * kTile;
-        const int64_t b = tile_ptr[T], e = tile_ptr[T + 1];
-        const int64_t width = (e - b) / kTile;
-        if (threadIdx.x == 0 && T + 2 < ntiles) {
-            prefetch_range(scol, sizeof(int32_t), tile_ptr[T + 2], tile_ptr[T + 3]);
-            prefetch_range(sval, sizeof(CT), tile_ptr[T + 2], tile_ptr[T + 3]);
-            prefetch_range(G, sizeof(CT), (T + 2) * kTile * kTile, (T + 3) * kTile * kTile);
-        }
-        // issue the loads of G_T (column-major) and v_T now; they are consumed
-        // after phase A, so their latency overlaps it
+        const int64_t b = tile_ptr[T];
+        const int64_t width = (tile_ptr[T + 1] - b) / kTile;
+        // loads of G_T (column-major) and v_T, consumed after phase A
         constexpr int kGPerThread = kTile * kTile / (kTileWarps * 32);
         CT greg[kGPerThread];
 #pragma unroll
-        for (int q = 0; q < kGPerThread; ++q) greg[q] = __ldcs(G + T * kTile * kTile + q * blockDim.x + threadIdx.x);
+        for (int q = 0; q < kGPerThread; ++q)
+            greg[q] = __ldcs(G + T * kTile * kTile + q * (kTileWarps * 32) + threadIdx.x);
         CT vreg = O::zero();
         if (warp == 0 && t0 + lane < N) vreg = __ldcg(v + (forward ? t0 + lane : N - 1 - (t0 + lane)));
-        // phase A: warp w takes a contiguous run of the slots of E_T; loads are
-        // batched eight deep so that their latencies overlap
-        const int64_t per = (width + kTileWarps - 1) / kTileWarps;
-        const int64_t k0 = warp * per, k1 = (k0 + per < width) ? k0 + per : width;
-        CT acc = O::zero(), acc2 = O::zero();
-        auto gather = [&](int32_t tj) -> CT {
-            return (t0 - tj <= WIN - kTile) ? win[tj & (WIN - 1)] : __ldcg(z + (forward ? tj : N - 1 - tj));
-        };
-        int64_t k = k0;
-        for (; k + 8 <= k1; k += 8) {
-            int32_t tj[8];
-            CT a[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int64_t idx = b + (k + u) * kTile + lane;
-                tj[u] = __ldcs(scol + idx);
-                a[u] = __ldcs(sval + idx);
+        // phase A over the streamed chunks of E_T
+        CT acc = O::zero();
+        bool ok = true;
+        for (int64_t c = 0; c < width; c += kChunkSlots, ++g) {
+            const int ns = (int)((width - c) < kChunkSlots ? (width - c) : kChunkSlots);
+            const int stage = (int)(g % STAGES);
+            if (!wait_phase(&full[stage], (uint32_t)((g / STAGES) & 1), &abort_flag)) ok = false;
+            if (ok) {
+                const int32_t *cs = col_s + stage * kChunkSlots * kTile;
+                const CT *vs = val_s + stage * kChunkSlots * kTile;
+                for (int q = warp; q < ns; q += kTileWarps) {
+                    const int32_t tj = cs[q * kTile + lane];
+                    const CT xj = (t0 - tj <= WIN - kTile) ? win[tj & (WIN - 1)]
+                                                           : __ldcg(z + (forward ? tj : N - 1 - tj));
+                    acc = O::fma(vs[q * kTile + lane], xj, acc);
+                }
             }
-            CT xs[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) xs[u] = gather(tj[u]);
-#pragma unroll
-            for (int u = 0; u < 8; u += 2) {
-                acc = O::fma(a[u], xs[u], acc);
-                acc2 = O::fma(a[u + 1], xs[u + 1], acc2);
-            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[stage]);
         }
-        for (; k < k1; ++k) {
-            const int64_t idx = b + k * kTile + lane;
-            acc = O::fma(__ldcs(sval + idx), gather(__ldcs(scol + idx)), acc);
-        }
-        acc = O::add(acc, acc2);
         part[warp * kTile + lane] = acc;
 #pragma unroll
-        for (int q = 0; q < kGPerThread; ++q) gs[q * blockDim.x + threadIdx.x] = greg[q];
-        __syncthreads();
+        for (int q = 0; q < kGPerThread; ++q) gs[q * (kTileWarps * 32) + threadIdx.x] = greg[q];
+        consumer_barrier();
         // phase B: x_T = G_T (v_T - sum of partials)
         if (warp == 0) {
             const int64_t t = t0 + lane;
@@ -164,12 +218,13 @@ tile_sweep(int64_t N, int64_t ntiles, int forward, const int64_t *__restrict__ t
                 yc.y = __shfl_sync(0xffffffffu, y.y, c);
                 x = O::fma(gs[c * kTile + lane], yc, x);
             }
+            if (abort_flag) x.x = x.y = __int_as_float(0x7fc00000);  // a timed-out wait shows up as NaN
             if (t < N) {
                 win[t & (WIN - 1)] = x;
                 z[r] = x;
             }
         }
-        __syncthreads();
+        consumer_barrier();
     }
 }
 
@@ -309,24 +364,25 @@ void to_c128(const float2 *v, int64_t N, double2 *out, cudaStream_t s) {
     OM_CHECK_LAUNCH();
 }
 
-template <class CT, int WIN>
+template <class CT, int WIN, int STAGES>
 static void launch_tile(const TilePlan &P, const CT *val, const CT *G, const CT *v, CT *z, cudaStream_t s) {
     if (P.ntiles == 0) return;
-    const size_t smem = sizeof(CT) * (WIN + kTileWarps * kTile + kTile * kTile);
-    auto k = tile_sweep<CT, WIN>;
+    const size_t smem = sizeof(int32_t) * STAGES * kChunkSlots * kTile + sizeof(CT) * STAGES * kChunkSlots * kTile +
+                        sizeof(CT) * (WIN + kTileWarps * kTile + kTile * kTile) + 2 * STAGES * sizeof(uint64_t);
+    auto k = tile_sweep<CT, WIN, STAGES>;
     OM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ProfScope prof(PROF_SWEEP, s);
-    k<<<1, kTileWarps * 32, smem, s>>>(P.N, P.ntiles, P.forward ? 1 : 0, P.tile_ptr.p, P.col.p, val, G, v, z);
+    k<<<1, (kTileWarps + 1) * 32, smem, s>>>(P.N, P.ntiles, P.forward ? 1 : 0, P.tile_ptr.p, P.col.p, val, G, v, z);
     omss::note_launch();
     OM_CHECK_LAUNCH();
 }
 
 void tile_sweep_c64(const TilePlan &P, const float2 *v, float2 *z, cudaStream_t s) {
-    launch_tile<float2, 16384>(P, P.val32.p, P.G32.p, v, z, s);
+    launch_tile<float2, 8192, 8>(P, P.val32.p, P.G32.p, v, z, s);
 }
 void tile_sweep_c128(const TilePlan &P, const double2 *v, double2 *z, cudaStream_t s) {
     OM_REQUIRE(P.ntiles == 0 || P.val64.p != nullptr, "complex128 sweep data was not built for this factor");
-    launch_tile<double2, 8192>(P, P.val64.p, P.G64.p, v, z, s);
+    launch_tile<double2, 4096, 4>(P, P.val64.p, P.G64.p, v, z, s);
 }
 
 void precond_apply(const om_ilu &M, bool conj_transpose, bool fp64, const double2 *v, double2 *z, float2 *tmp32,
