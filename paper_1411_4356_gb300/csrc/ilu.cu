@@ -114,15 +114,23 @@ void ilut_worker(IlutShared &S) {
             }
             w[k] = m;
             const int64_t ub = S.slot[k], ue = ub + S.ucnt[k];
+            // w -= m * (row k of U), in real arithmetic: the library complex
+            // product guards against NaN operands on every call, which costs
+            // several times the arithmetic in this innermost loop
+            const double mr = m.real(), mi = m.imag();
+            double *wd = reinterpret_cast<double *>(w.data());
+            const double *ud = reinterpret_cast<const double *>(S.uva.data());
             for (int64_t e = ub; e < ue; ++e) {
-                int32_t c = S.uci[e];
+                const int32_t c = S.uci[e];
                 if (!in_row[c]) {
                     in_row[c] = 1;
                     w[c] = 0;
                     present.push_back(c);
                     if (c < i) pending.push(c);
                 }
-                w[c] -= m * S.uva[e];
+                const double ur = ud[2 * e], ui = ud[2 * e + 1];
+                wd[2 * c] -= mr * ur - mi * ui;
+                wd[2 * c + 1] -= mr * ui + mi * ur;
             }
         }
         lo.clear();

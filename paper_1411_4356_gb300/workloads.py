@@ -61,10 +61,10 @@ LARGE = Workload("large_20x200", SystemParams(20, 200, 1.0, -1.0, 0.5, 1.5, 0.5,
 ADJOINT = Workload("adjoint_12x100", SystemParams(12, 100, 1.0, -1.0, 0.5, 1.0, 0.4, 1e4, 0.5),
                    droptol=1e-4, fill=10.0, restart=30, tol=1e-10)
 # batched sweep base parameters (N_c = 6; Delta and N_m drawn per system).
-# ILUT(1e-4, 40): with a fill cap of 20 several draws give an unstable factor.
+# ILUT(1e-5, 60): with caps of 20 and 40 some draws give an unstable factor.
 BATCH_BASE = SystemParams(6, 20, 1.0, 0.0, 0.4, 0.8, 0.2, 1e3, 0.2)
 BATCH_NM = (20, 30, 40, 60)
-BATCH = Workload("batched_6xNm", BATCH_BASE, droptol=1e-4, fill=40.0, restart=30, tol=1e-10)
+BATCH = Workload("batched_6xNm", BATCH_BASE, droptol=1e-5, fill=60.0, restart=30, tol=1e-10)
 
 
 def batched_draws(count: int = 512, seed: int = 4356):
