@@ -47,6 +47,8 @@ def parse():
                     help="mid: the 360,000-row FP64 system (default); batched: the parameter sweep "
                          "(N_c = 6, N_m in {20, 30, 40, 60}), solve phase timed")
     ap.add_argument("--systems", type=int, default=64, help="systems of the sweep for --workload batched")
+    ap.add_argument("--concurrency", type=int, default=0,
+                    help="--workload batched: 0 = lock-step engine, k > 0 = k concurrent single solves")
     return ap.parse_args()
 
 
@@ -130,6 +132,18 @@ def sweep_traffic_per_entry(kernel_hash: str):
     return d.get("dram_bytes_per_factor_entry")
 
 
+def max_over_ranks(values, world: int, dist=None):
+    """Element-wise maximum of per-rank timings (every rank gets the result)."""
+    if world <= 1:
+        return list(values)
+    import torch
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor(list(values), dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
 # ----------------------------------------------------------------- GPU arm
 def run_omss(args):
     import torch
@@ -150,12 +164,12 @@ def run_omss(args):
     rho_host = torch.empty(n * n, dtype=torch.complex128, pin_memory=True)
     stream = torch.cuda.current_stream()
 
-    def step(readback: bool):
+    def step(readback: bool, precision: int = w.precision):
         A = api.build_liouvillian(p, w.trace_mode, w.nth_floor)
         Ar, perm = api.permute(A)
         A.free()
         M = api.ilu_factor(Ar, w.droptol, w.fill)
-        _, info = api.steady_state_solve(Ar, M, perm, restart=w.restart, tol=w.tol, precision=w.precision,
+        _, info = api.steady_state_solve(Ar, M, perm, restart=w.restart, tol=w.tol, precision=precision,
                                          rho_out=rho_dev)
         obs = api.observables(p.Nc, p.Nm, rho_dev)
         if readback:
@@ -174,39 +188,45 @@ def run_omss(args):
         if world > 1:
             dist.barrier()
 
-    # ---- timed region: device-resident inputs (value)
+    # ---- timed region.  Each step: the device pipeline between two CUDA
+    # events (value: inputs resident), then rho read back to pinned host
+    # memory and the host synchronised (e2e: wall clock over the whole loop).
     clocks = ClockSampler(local)
     barrier()
     torch.cuda.synchronize()
     clocks.start()
     launches0 = api.kernel_launches()
     api.profile(True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    stats = [step(False) for _ in range(args.steps)]
-    e1.record(stream)
-    torch.cuda.synchronize()
+    device_s = 0.0
+    stats = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = step(False)
+        e1.record(stream)
+        rho_host.copy_(rho_dev, non_blocking=True)
+        torch.cuda.synchronize()
+        device_s += e0.elapsed_time(e1) / 1e3
+        stats.append(st)
+    e2e_elapsed = time.perf_counter() - t0
     barrier()
     launches = api.kernel_launches() - launches0
     sweep_ms, sweep_n = api.profile_read(api.PROF_SWEEP)
     spmv_ms, spmv_n = api.profile_read(api.PROF_SPMV)
     api.profile(False)
-    elapsed = e0.elapsed_time(e1) / 1e3
-    # ---- end to end through the same API, result read back to pinned host memory
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step(True)
-        torch.cuda.synchronize()
-    e2e_elapsed = time.perf_counter() - t0
-    barrier()
     clk = clocks.stop()
+    rho64 = rho_dev.clone()
+    # ---- the same workload with the mixed-precision solve (one step)
+    m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    m0.record(stream)
+    mstat = step(False, precision=1)
+    m1.record(stream)
+    torch.cuda.synchronize()
+    mixed_s = m0.elapsed_time(m1) / 1e3
+    mixed_err = float((rho_dev - rho64).abs().max())
 
-    t = torch.tensor([elapsed, e2e_elapsed], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed, e2e_elapsed = float(t[0]), float(t[1])
+    elapsed, e2e_elapsed, mixed_s = max_over_ranks([device_s, e2e_elapsed, mixed_s], world, dist)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -215,6 +235,10 @@ def run_omss(args):
     N, nnz = s0["N"], s0["nnz"]
     solves = args.steps * world
     value = solves / elapsed
+    mixed = {"value": world / mixed_s, "unit": "solves/s", "solve_s": mstat["solve_s"],
+             "iterations": mstat["iterations"], "eta": mstat["eta"],
+             "max_abs_diff_vs_fp64_rho": mixed_err,
+             "note": "same step with precision = 1: complex64 inner GMRES (SpMV, basis, sweeps) in FP64 refinement"}
 
     # algorithmic bytes: complex64 sweeps stream the strict factor (8-byte value
     # + 4-byte column), the row pointers and the vectors once per launch
@@ -264,6 +288,7 @@ def run_omss(args):
                              f"levels L/U = {s0['levels'][0]}/{s0['levels'][1]}"},
         "e2e": {"value": solves / e2e_elapsed, "unit": "solves/s", "h2d_bytes_per_step": 72,
                 "d2h_bytes_per_step": 16 * n * n},
+        "mixed": mixed,
         "gpu_launches": int(launches),
         "clocks": clk,
         "krylov_gbs": krylov_bytes / solve_s / 1e9,
@@ -359,8 +384,12 @@ def run_batched(args):
         A.free()
         systems.append((Ar, api.ilu_factor(Ar, BATCH.droptol, BATCH.fill), perm))
     setup_s = time.perf_counter() - t0
+    def solve():
+        return api.steady_state_solve_batched(systems, restart=BATCH.restart, tol=BATCH.tol,
+                                              concurrency=args.concurrency)
+
     for _ in range(args.warmup):
-        api.steady_state_solve_batched(systems, restart=BATCH.restart, tol=BATCH.tol)
+        solve()
     torch.cuda.synchronize()
     clocks = ClockSampler(0)
     clocks.start()
@@ -368,19 +397,27 @@ def run_batched(args):
     api.profile(True)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        _, infos = api.steady_state_solve_batched(systems, restart=BATCH.restart, tol=BATCH.tol)
+        _, infos = solve()
     torch.cuda.synchronize()
     elapsed = time.perf_counter() - t0
     sweep_ms, sweep_n = api.profile_read(api.PROF_SWEEP)
     api.profile(False)
     launches = api.kernel_launches() - launches0
     clk = clocks.stop()
-    # algorithmic sweep bytes: each solve's launches stream its factors once each
+    # algorithmic bytes of the preconditioner applications: every application
+    # streams the system's complex64 factors once (12 B per entry with its
+    # column) plus the vector conversions; one per Krylov iteration
     swept = 0.0
     for (Ar, M, perm), info in zip(systems, infos):
         per_apply = 12 * (M.nnz_l + M.nnz_u - Ar.N) + 2 * (8 * (Ar.N + 1) + 16 * Ar.N)
-        swept += per_apply * (info.iterations + 0)
+        swept += per_apply * info.iterations
     swept *= args.steps
+    engine = "lock-step" if args.concurrency <= 0 else f"{args.concurrency} concurrent streams"
+    kernel = ("b_precond: one launch per Krylov step, one block per system" if args.concurrency <= 0
+              else "tile_sweep, concurrent over the batch")
+    # lock-step: the preconditioner launches are timed themselves; streams:
+    # only the wall clock of the batch bounds them
+    sweep_s = sweep_ms / 1e3 if args.concurrency <= 0 and sweep_ms > 0 else elapsed
     peak, peak_kind = measured_peaks()
     bad = [i.status for i in infos if i.status != 0]
     line = {"metric": METRIC, "value": len(systems) * args.steps / elapsed, "unit": "solves/s",
@@ -390,10 +427,10 @@ def run_batched(args):
             "config": {"workload": BATCH.name, "systems": len(systems), "Nc": 6,
                        "Nm": sorted({p.Nm for p in params}), "rows_total": sum(A.N for A, _, _ in systems),
                        "droptol": BATCH.droptol, "fill_cap": BATCH.fill, "restart": BATCH.restart, "tol": BATCH.tol,
-                       "timed": "batched solve phase (setup outside)", "setup_s": setup_s},
-            "roofline": {"bound": "hbm", "kernel": "tile_sweep, concurrent over the batch",
-                         "achieved": swept / elapsed / 1e9, "peak": peak, "unit": "GB/s",
-                         "frac": swept / elapsed / 1e9 / peak, "peak_kind": f"{peak_kind} copy bandwidth",
+                       "timed": "batched solve phase (setup outside)", "setup_s": setup_s, "engine": engine},
+            "roofline": {"bound": "hbm", "kernel": kernel,
+                         "achieved": swept / sweep_s / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": swept / sweep_s / 1e9 / peak, "peak_kind": f"{peak_kind} copy bandwidth",
                          "traffic": None, "sweep_launches": sweep_n,
                          "sweep_device_ms_sum": sweep_ms},
             "gpu_launches": int(launches), "clocks": clk,

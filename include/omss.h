@@ -176,15 +176,22 @@ om_status om_steady_state_adjoint(const om_matrix *A_rcm, const om_ilu *M, const
 
 /* ---- batched steady states --------------------------------------------------
  * Solves `count` independent systems (a parameter sweep, Sec. IV) with
- * om_steady_state_solve semantics, up to `concurrency` at a time (<= 0:
- * twice the SM count), each on its own stream driven by its own host thread,
- * so that the single-block sweeps of different systems run on different
- * SMs at once.  A_rcm[i], M[i], perm_dev[i], rho_dev[i] are as for
- * om_steady_state_solve (x0 is not taken); opts applies to all.  status[i]
- * (HOST, count entries) receives each solve's status and info[i] (HOST, may
- * be NULL) its statistics.  Inputs written on `stream` before the call are
- * honoured, and the results are ordered before later work on `stream`.
- * Returns OM_OK if the batch ran (check status[]), else OM_EINVAL/OM_ECUDA. */
+ * om_steady_state_solve semantics.  A_rcm[i], M[i], perm_dev[i], rho_dev[i]
+ * are as for om_steady_state_solve (x0 is not taken; systems may differ in
+ * size); opts applies to all.  status[i] (HOST, count entries) receives each
+ * solve's status and info[i] (HOST, may be NULL) its statistics
+ * (info[i].seconds is the time of the whole batch).
+ * concurrency <= 0: lock-step engine.  One flexible GMRES(m) advances all
+ * systems together: each Krylov step is one launch per kernel over every
+ * system still iterating, the preconditioner kernel running one thread block
+ * per system (complex64 L and U sweeps), and systems retire as they converge.
+ * Requires opts->precision == 0, opts->precond_fp64 == 0, restart <= 64.
+ * concurrency > 0: up to `concurrency` calls of om_steady_state_solve at a
+ * time, each on its own stream driven by its own host thread (any opts).
+ * Inputs written on `stream` before the call are honoured, and the results
+ * are ordered before later work on `stream`.
+ * Returns OM_OK if the batch ran (check status[]), else OM_EINVAL, OM_ENOMEM
+ * or OM_ECUDA. */
 om_status om_steady_state_solve_batched(int32_t count, const om_matrix *const *A_rcm,
                                         const om_ilu *const *M, const int32_t *const *perm_dev,
                                         const om_solve_opts *opts, double *const *rho_dev,

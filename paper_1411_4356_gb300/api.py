@@ -285,8 +285,11 @@ def steady_state(theta: torch.Tensor, base: SystemParams, **options) -> torch.Te
 
 def steady_state_solve_batched(systems, restart: int = 30, max_iters: int = 5000, tol: float = 1e-10,
                                precision: int = 0, concurrency: int = 0, stream=None):
-    """Solve many (A_rcm, M, perm) systems concurrently (om_steady_state_solve_batched).
+    """Solve many (A_rcm, M, perm) systems together (om_steady_state_solve_batched).
 
+    concurrency <= 0 runs the lock-step engine (one launch per kernel and
+    Krylov step for all systems; precision 0 only); concurrency > 0 runs that
+    many single solves at a time on their own streams.
     Returns ([rho n x n CUDA tensors], [SolveInfo])."""
     lib = _lib.load()
     count = len(systems)

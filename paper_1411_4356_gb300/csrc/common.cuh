@@ -162,6 +162,7 @@ struct om_matrix {
 // dense inverse of the 32 x 32 diagonal block (column-major).
 struct TilePlan {
     int64_t N = 0, ntiles = 0, padded_entries = 0;
+    int64_t nchunks = 0;           // streamed chunks of 32 slots over all tiles
     bool forward = true;
     omss::DBuf<int64_t> tile_ptr;  // ntiles + 1 offsets into col / val
     omss::DBuf<int32_t> col;       // sweep-order column t_j

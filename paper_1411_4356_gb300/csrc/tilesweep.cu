@@ -35,197 +35,27 @@
 #include <thread>
 
 #include "common.cuh"
+#include "tilesweep.cuh"
 
 namespace omss {
+using tsw::kChunkSlots;
+using tsw::kTile;
+using tsw::kTileWarps;
 namespace {
 
-constexpr int kTile = 32;
-constexpr int kTileWarps = 16;
-
-template <class CT>
-struct TOps;
-template <>
-struct TOps<double2> {
-    __device__ static double2 zero() { return make_double2(0, 0); }
-    __device__ static double2 fma(double2 a, double2 x, double2 acc) {
-        return make_double2(__fma_rn(a.x, x.x, __fma_rn(-a.y, x.y, acc.x)), __fma_rn(a.x, x.y, __fma_rn(a.y, x.x, acc.y)));
-    }
-    __device__ static double2 sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-    __device__ static double2 add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-};
-template <>
-struct TOps<float2> {
-    __device__ static float2 zero() { return make_float2(0, 0); }
-    __device__ static float2 fma(float2 a, float2 x, float2 acc) {
-        return make_float2(__fmaf_rn(a.x, x.x, __fmaf_rn(-a.y, x.y, acc.x)), __fmaf_rn(a.x, x.y, __fmaf_rn(a.y, x.x, acc.y)));
-    }
-    __device__ static float2 sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-    __device__ static float2 add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-};
-
-__device__ inline uint32_t smem_u32(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
-__device__ inline void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ inline void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ inline void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ inline bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// global -> shared bulk copy (TMA, no tensor map) completing on an mbarrier
-__device__ inline void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-__device__ inline uint64_t now_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ inline void consumer_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(kTileWarps * 32) : "memory"); }
-
-// Waits for an mbarrier phase; gives up after 2 s or once `abort` is set,
-// setting `abort` so that every other wait of the block returns at once.
-__device__ inline bool wait_phase(uint64_t *bar, uint32_t parity, volatile int *abort) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t start = now_ns();
-    for (;;) {
-        if (*abort) return false;
-        if (mbar_try_wait(bar, parity)) return true;
-        if (now_ns() - start > 2000000000ull) {
-            *abort = 1;
-            return false;
-        }
-    }
-}
-
-constexpr int kChunkSlots = 32;  // slots (of 32 rows) per streamed chunk
 
 // v, z: natural-order vectors (index r); the tile data is in sweep order t.
-// Warps 0..15 compute; warp 16 streams the tiles' slots into a ring of
-// STAGES shared-memory buffers with bulk copies (full / empty mbarriers).
 template <class CT, int WIN, int STAGES>
 __global__ void __launch_bounds__((kTileWarps + 1) * 32, 1)
 tile_sweep(int64_t N, int64_t ntiles, int forward, const int64_t *__restrict__ tile_ptr,
            const int32_t *__restrict__ scol, const CT *__restrict__ sval, const CT *__restrict__ G,
            const CT *v, CT *z) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    int32_t *col_s = reinterpret_cast<int32_t *>(smem_raw);
-    CT *val_s = reinterpret_cast<CT *>(smem_raw + sizeof(int32_t) * STAGES * kChunkSlots * kTile);
-    CT *win = val_s + STAGES * kChunkSlots * kTile;  // WIN rows of x, by t
-    CT *part = win + WIN;                             // kTileWarps x 32 partial sums
-    CT *gs = part + kTileWarps * kTile;               // 32 x 32 inverse of the tile
-    uint64_t *full = reinterpret_cast<uint64_t *>(gs + kTile * kTile);
-    uint64_t *empty = full + STAGES;
-    __shared__ volatile int abort_flag;
-    using O = TOps<CT>;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) {
-        abort_flag = 0;
-        for (int q = 0; q < STAGES; ++q) {
-            mbar_init(&full[q], 1);
-            mbar_init(&empty[q], kTileWarps);
-        }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
+    tsw::SweepSmem<CT, WIN, STAGES> sm;
+    sm.carve(smem_raw);
+    sm.init();
     __syncthreads();
-
-    if (warp == kTileWarps) {  // producer
-        if (lane == 0) {
-            int64_t g = 0;
-            for (int64_t T = 0; T < ntiles && !abort_flag; ++T) {
-                const int64_t b = tile_ptr[T];
-                const int64_t width = (tile_ptr[T + 1] - b) / kTile;
-                for (int64_t c = 0; c < width; c += kChunkSlots, ++g) {
-                    const int ns = (int)((width - c) < kChunkSlots ? (width - c) : kChunkSlots);
-                    const int stage = (int)(g % STAGES);
-                    const uint32_t use = (uint32_t)(g / STAGES);
-                    if (g >= STAGES && !wait_phase(&empty[stage], (use - 1) & 1, &abort_flag)) return;
-                    const uint32_t bc = (uint32_t)(ns * kTile * sizeof(int32_t));
-                    const uint32_t bv = (uint32_t)(ns * kTile * sizeof(CT));
-                    mbar_expect_tx(&full[stage], bc + bv);
-                    bulk_g2s(col_s + stage * kChunkSlots * kTile, scol + b + c * kTile, bc, &full[stage]);
-                    bulk_g2s(val_s + stage * kChunkSlots * kTile, sval + b + c * kTile, bv, &full[stage]);
-                }
-            }
-        }
-        return;
-    }
-
-    int64_t g = 0;
-    for (int64_t T = 0; T < ntiles; ++T) {
-        const int64_t t0 = T * kTile;
-        const int64_t b = tile_ptr[T];
-        const int64_t width = (tile_ptr[T + 1] - b) / kTile;
-        // loads of G_T (column-major) and v_T, consumed after phase A
-        constexpr int kGPerThread = kTile * kTile / (kTileWarps * 32);
-        CT greg[kGPerThread];
-#pragma unroll
-        for (int q = 0; q < kGPerThread; ++q)
-            greg[q] = __ldcs(G + T * kTile * kTile + q * (kTileWarps * 32) + threadIdx.x);
-        CT vreg = O::zero();
-        if (warp == 0 && t0 + lane < N) vreg = __ldcg(v + (forward ? t0 + lane : N - 1 - (t0 + lane)));
-        // phase A over the streamed chunks of E_T
-        CT acc = O::zero();
-        bool ok = true;
-        for (int64_t c = 0; c < width; c += kChunkSlots, ++g) {
-            const int ns = (int)((width - c) < kChunkSlots ? (width - c) : kChunkSlots);
-            const int stage = (int)(g % STAGES);
-            if (!wait_phase(&full[stage], (uint32_t)((g / STAGES) & 1), &abort_flag)) ok = false;
-            if (ok) {
-                const int32_t *cs = col_s + stage * kChunkSlots * kTile;
-                const CT *vs = val_s + stage * kChunkSlots * kTile;
-                for (int q = warp; q < ns; q += kTileWarps) {
-                    const int32_t tj = cs[q * kTile + lane];
-                    const CT xj = (t0 - tj <= WIN - kTile) ? win[tj & (WIN - 1)]
-                                                           : __ldcg(z + (forward ? tj : N - 1 - tj));
-                    acc = O::fma(vs[q * kTile + lane], xj, acc);
-                }
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[stage]);
-        }
-        part[warp * kTile + lane] = acc;
-#pragma unroll
-        for (int q = 0; q < kGPerThread; ++q) gs[q * (kTileWarps * 32) + threadIdx.x] = greg[q];
-        consumer_barrier();
-        // phase B: x_T = G_T (v_T - sum of partials)
-        if (warp == 0) {
-            const int64_t t = t0 + lane;
-            const int64_t r = forward ? t : N - 1 - t;
-            CT y = O::zero();
-            if (t < N) {
-                y = vreg;
-                for (int w = 0; w < kTileWarps; ++w) y = O::sub(y, part[w * kTile + lane]);
-            }
-            CT x = O::zero();
-#pragma unroll 8
-            for (int c = 0; c < kTile; ++c) {
-                CT yc;
-                yc.x = __shfl_sync(0xffffffffu, y.x, c);
-                yc.y = __shfl_sync(0xffffffffu, y.y, c);
-                x = O::fma(gs[c * kTile + lane], yc, x);
-            }
-            if (abort_flag) x.x = x.y = __int_as_float(0x7fc00000);  // a timed-out wait shows up as NaN
-            if (t < N) {
-                win[t & (WIN - 1)] = x;
-                z[r] = x;
-            }
-        }
-        consumer_barrier();
-    }
+    tsw::sweep_block<CT, WIN, STAGES>(sm, N, ntiles, forward, tile_ptr, scol, sval, G, v, z, 0);
 }
 
 }  // namespace
@@ -335,6 +165,11 @@ void build_tile_plan(TilePlan &P, int64_t N, const std::vector<int64_t> &rp, con
             OM_CUDA_TRY(cudaMemcpyAsync(P.G64.p, G.data(), sizeof(double2) * G.size(), cudaMemcpyHostToDevice, s));
     }
     P.padded_entries = total;
+    P.nchunks = 0;
+    for (int64_t T = 0; T < ntiles; ++T) {
+        const int64_t width = (tptr[T + 1] - tptr[T]) / kTile;
+        P.nchunks += (width + kChunkSlots - 1) / kChunkSlots;
+    }
     OM_CUDA_TRY(cudaStreamSynchronize(s));  // host staging vectors go out of scope
 }
 
@@ -367,8 +202,7 @@ void to_c128(const float2 *v, int64_t N, double2 *out, cudaStream_t s) {
 template <class CT, int WIN, int STAGES>
 static void launch_tile(const TilePlan &P, const CT *val, const CT *G, const CT *v, CT *z, cudaStream_t s) {
     if (P.ntiles == 0) return;
-    const size_t smem = sizeof(int32_t) * STAGES * kChunkSlots * kTile + sizeof(CT) * STAGES * kChunkSlots * kTile +
-                        sizeof(CT) * (WIN + kTileWarps * kTile + kTile * kTile) + 2 * STAGES * sizeof(uint64_t);
+    const size_t smem = tsw::SweepSmem<CT, WIN, STAGES>::bytes();
     auto k = tile_sweep<CT, WIN, STAGES>;
     OM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ProfScope prof(PROF_SWEEP, s);
