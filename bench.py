@@ -119,11 +119,11 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def sweep_traffic_per_entry(kernel_hash: str):
-    """DRAM bytes per stored factor entry of one sweep launch, from the
+def sweep_traffic_per_entry(kernel_hash: str, name: str = "sweep_traffic.json"):
+    """DRAM bytes per stored factor entry of one sweep launch, from a
     committed ncu summary of the 40,000-row case, or None if the kernel
     source changed since the counters were taken."""
-    path = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
@@ -165,9 +165,11 @@ def run_omss(args):
     stream = torch.cuda.current_stream()
 
     def step(readback: bool, precision: int = w.precision):
+        h0 = time.perf_counter()
         A = api.build_liouvillian(p, w.trace_mode, w.nth_floor)
         Ar, perm = api.permute(A)
         A.free()
+        h1 = time.perf_counter()
         M = api.ilu_factor(Ar, w.droptol, w.fill)
         _, info = api.steady_state_solve(Ar, M, perm, restart=w.restart, tol=w.tol, precision=precision,
                                          rho_out=rho_dev)
@@ -175,7 +177,8 @@ def run_omss(args):
         if readback:
             rho_host.copy_(rho_dev, non_blocking=True)
         stats = dict(nnz=Ar.nnz, N=Ar.N, nnz_l=M.nnz_l, nnz_u=M.nnz_u, fill=M.fill, levels=(M.levels_l, M.levels_u),
-                     iterations=info.iterations, eta=info.eta, solve_s=info.seconds, obs=obs)
+                     iterations=info.iterations, eta=info.eta, solve_s=info.seconds, obs=obs,
+                     build_permute_s=h1 - h0, ilu_s=M.timings)
         M.free()
         Ar.free()
         return stats
@@ -213,8 +216,12 @@ def run_omss(args):
     barrier()
     launches = api.kernel_launches() - launches0
     sweep_ms, sweep_n = api.profile_read(api.PROF_SWEEP)
+    split_ms, split_n = api.profile_read(api.PROF_SPLIT)
     spmv_ms, spmv_n = api.profile_read(api.PROF_SPMV)
     api.profile(False)
+    split = split_n > 0
+    if split:  # the sweeps ran split over the SMs
+        sweep_ms, sweep_n = split_ms, split_n
     clk = clocks.stop()
     rho64 = rho_dev.clone()
     # ---- the same workload with the mixed-precision solve (one step)
@@ -249,8 +256,9 @@ def run_omss(args):
     sweep_avg_ms = sweep_ms / max(sweep_n, 1)
     achieved = sweep_bytes / (sweep_ms / 1e3) / 1e9 if sweep_ms > 0 else 0.0
     peak, peak_kind = measured_peaks()
-    khash = source_hash(os.path.join(ROOT, "paper_1411_4356_gb300", "csrc", "tilesweep.cu"))
-    per_entry = sweep_traffic_per_entry(khash)
+    kfile = "splitsweep.cu" if split else "tilesweep.cu"
+    khash = source_hash(os.path.join(ROOT, "paper_1411_4356_gb300", "csrc", kfile))
+    per_entry = sweep_traffic_per_entry(khash, "split_sweep_traffic.json" if split else "sweep_traffic.json")
     # scaled to one launch of this workload by the factor entries it streams
     traffic = per_entry * (nnz_l + nnz_u_strict) / 2.0 if per_entry else None
     # Krylov bytes per solve: SpMV (c128 value + column, row pointers, x, y),
@@ -280,19 +288,24 @@ def run_omss(args):
                    "krylov": "FP64 flexible GMRES", "preconditioner": "ILUT, complex64 sweeps",
                    "parallelism": f"replicas x{world}",
                    "l2": "working set (ILU factors) larger than L2; no flush needed"},
-        "roofline": {"bound": "hbm", "kernel": "tile_sweep (complex64 L and U sweeps)",
+        "roofline": {"bound": "hbm",
+                     "kernel": ("split_sweep (complex64 L and U sweeps over all SMs)" if split
+                                else "tile_sweep (complex64 L and U sweeps, one block)"),
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
                      "traffic": traffic, "avg_launch_ms": sweep_avg_ms, "launches": sweep_n,
-                     "note": "one thread block per sweep: bound by the dependency depth of the factors, "
-                             f"levels L/U = {s0['levels'][0]}/{s0['levels'][1]}"},
+                     "note": ("main block runs the dependency chain over the near band, helper blocks the older "
+                              "tiles; " if split else "one thread block per sweep; ") +
+                             f"dependency depth of the factors L/U = {s0['levels'][0]}/{s0['levels'][1]} levels"},
         "e2e": {"value": solves / e2e_elapsed, "unit": "solves/s", "h2d_bytes_per_step": 72,
                 "d2h_bytes_per_step": 16 * n * n},
         "mixed": mixed,
         "gpu_launches": int(launches),
         "clocks": clk,
         "krylov_gbs": krylov_bytes / solve_s / 1e9,
-        "phase_s": {"solve": solve_s, "setup_and_rest": elapsed / args.steps - solve_s},
+        "phase_s": {"solve": solve_s, "setup_and_rest": elapsed / args.steps - solve_s,
+                    "build_permute": sum(st["build_permute_s"] for st in stats) / len(stats),
+                    **{"ilu_" + k: sum(st["ilu_s"][k] for st in stats) / len(stats) for k in stats[0]["ilu_s"]}},
         "iterations": its,
         "eta": s0["eta"],
         "fill": s0["fill"],

@@ -147,6 +147,10 @@ om_status om_ilu_factor(const om_matrix *A_rcm, double droptol, double fill, int
 /* Statistics of a factorisation (any out pointer may be NULL). */
 om_status om_ilu_info(const om_ilu *M, int64_t *nnz_l, int64_t *nnz_u, int64_t *n_guarded,
                       int64_t *levels_l, int64_t *levels_u);
+/* Host wall-clock seconds of the phases of om_ilu_factor (HOST double[4]):
+ * copy of A to the host, ILUT, dependency depths, tiled layout and upload.
+ * Instrumentation; no counterpart in the paper. */
+om_status om_ilu_timings(const om_ilu *M, double seconds[4]);
 
 /* ---- Sec. IV: the steady state ----------------------------------------------
  * Solves L~_rcm x = P (w, 0, ...)^T by restarted GMRES(m) with right
@@ -204,7 +208,10 @@ om_status om_spmv(const om_matrix *A, const double *x, double *y, void *stream);
 /* z = (L U)^{-1} v, or (L U)^{-H} v, with DEVICE c128[N] vectors (z and v may
  * alias).  flags bit 0: sweep with the complex128 data (the factor must have
  * been built with it), else complex64; bit 1: apply the conjugate transpose
- * (the factor must keep the transposes).  Errors: OM_EINVAL, OM_ECUDA. */
+ * (the factor must keep the transposes); bit 2: run the complex64 sweeps in
+ * one thread block even where the split sweep over all SMs applies (the two
+ * differ only in the order of the complex64 sums).  The split sweep takes
+ * scratch from the stream-ordered allocator.  Errors: OM_EINVAL, OM_ECUDA. */
 om_status om_ilu_apply(const om_ilu *M, int32_t flags, const double *v, double *z,
                        void *stream);
 /* Allocation-free variant of om_ilu_apply.  The paper has no counterpart:
@@ -212,7 +219,8 @@ om_status om_ilu_apply(const om_ilu *M, int32_t flags, const double *v, double *
  * code whose device memory belongs to another allocator (a framework's
  * caching pool), and latency-critical code that must not enter the allocator
  * or risk the implicit device synchronisation of cudaMalloc/cudaFree.  It
- * computes the same z as om_ilu_apply (same flags, same DEVICE c128 vectors,
+ * computes the same z as om_ilu_apply with flag bit 2 (one-block sweeps; same
+ * flags otherwise, same DEVICE c128 vectors,
  * z and v may alias) but takes its scratch -- a complex64 work vector of at
  * most 1,048,576 rows and a status word -- from a static device array that
  * every GPU loading the library holds (8 MiB) until the process exits, and
@@ -229,8 +237,9 @@ om_status om_observables(int32_t Nc, int32_t Nm, const double *rho_dev, double o
 
 /* ---- instrumentation (no counterpart in the paper) -------------------------
  * om_kernel_launches: number of kernels the library has launched since it was
- * loaded.  om_profile(1) starts recording CUDA events around every triangular
- * sweep (category 0) and SpMV (category 1) launch, om_profile(0) stops, both
+ * loaded.  om_profile(1) starts recording CUDA events around every one-block
+ * triangular sweep (category 0), SpMV (category 1) and split sweep over all
+ * SMs (category 2) launch, om_profile(0) stops, both
  * discard earlier records; om_profile_read returns the summed device time
  * (milliseconds, HOST out) and launch count of a category, synchronising on
  * the recorded events. */

@@ -43,6 +43,7 @@ SIGNATURES = {
     "om_permute": (c_i32, [c_vp, c_vp, c_vp, ctypes.POINTER(c_vp)]),
     "om_ilu_factor": (c_i32, [c_vp, c_dbl, c_dbl, c_i32, c_vp, ctypes.POINTER(c_vp)]),
     "om_ilu_info": (c_i32, [c_vp] + [ctypes.POINTER(c_i64)] * 5),
+    "om_ilu_timings": (c_i32, [c_vp, ctypes.POINTER(c_dbl)]),
     "om_steady_state_solve": (c_i32, [c_vp, c_vp, c_vp, ctypes.POINTER(om_solve_opts), c_vp, c_vp,
                                       ctypes.POINTER(om_solve_info), c_vp]),
     "om_steady_state_adjoint": (c_i32, [c_vp, c_vp, c_vp, ctypes.POINTER(om_solve_opts), ctypes.POINTER(om_params),

@@ -84,6 +84,10 @@ class ILU:
         check(_lib.load().om_ilu_info(self._h, *[ctypes.byref(v) for v in vals]), "om_ilu_info")
         self.nnz_l, self.nnz_u, self.n_guarded, self.levels_l, self.levels_u = (v.value for v in vals)
         self.fill = (self.nnz_l + self.nnz_u) / nnz_a
+        t = (ctypes.c_double * 4)()
+        check(_lib.load().om_ilu_timings(self._h, t), "om_ilu_timings")
+        # host seconds: copy of A to the host, ILUT, dependency depths, tiled layout + upload
+        self.timings = dict(zip(("copy", "ilut", "depth", "layout"), list(t)))
 
     @property
     def handle(self):
@@ -203,10 +207,11 @@ def spmv(A: Matrix, x: torch.Tensor, stream=None) -> torch.Tensor:
 
 
 def ilu_apply(M: ILU, v: torch.Tensor, conj_transpose: bool = False, fp64: bool = False,
-              stream=None) -> torch.Tensor:
-    """z = (L U)^{-1} v (or (L U)^{-H} v); fp64 selects the complex128 sweeps."""
+              single_block: bool = False, stream=None) -> torch.Tensor:
+    """z = (L U)^{-1} v (or (L U)^{-H} v); fp64 selects the complex128 sweeps,
+    single_block keeps the complex64 sweeps in one thread block."""
     z = torch.empty_like(v)
-    flags = (1 if fp64 else 0) | (2 if conj_transpose else 0)
+    flags = (1 if fp64 else 0) | (2 if conj_transpose else 0) | (4 if single_block else 0)
     check(_lib.load().om_ilu_apply(M.handle, flags, _ptr(v.contiguous()), _ptr(z),
                                    ctypes.c_void_p(_stream(stream))), "om_ilu_apply")
     return z
@@ -226,7 +231,7 @@ def kernel_launches() -> int:
     return int(_lib.load().om_kernel_launches())
 
 
-PROF_SWEEP, PROF_SPMV = 0, 1
+PROF_SWEEP, PROF_SPMV, PROF_SPLIT = 0, 1, 2
 
 
 def profile(enable: bool) -> None:

@@ -658,6 +658,8 @@ void solve_streams(int32_t count, const om_matrix *const *A_rcm, const om_ilu *c
     std::atomic<int> next{0};
     auto worker = [&](int t) {
         cudaSetDevice(dev);
+        set_single_block_sweeps(true);  // concurrent sweeps: one block each
+
         for (;;) {
             const int i = next.fetch_add(1);
             if (i >= count) break;
@@ -666,6 +668,7 @@ void solve_streams(int32_t count, const om_matrix *const *A_rcm, const om_ilu *c
                                               reinterpret_cast<void *>(streams[t]));
             if (info) info[i] = local;
         }
+        set_single_block_sweeps(false);
         cudaEventRecord(done[t], streams[t]);
     };
     std::vector<std::thread> pool;

@@ -19,8 +19,8 @@ void set_error(const std::string &msg);
 void note_launch();
 
 // Kernel timing by CUDA events, active between om_profile(1) and om_profile(0).
-// Categories: 0 = triangular sweeps, 1 = SpMV.
-enum { PROF_SWEEP = 0, PROF_SPMV = 1, PROF_CATEGORIES = 2 };
+// Categories: 0 = one-block triangular sweeps, 1 = SpMV, 2 = split sweeps.
+enum { PROF_SWEEP = 0, PROF_SPMV = 1, PROF_SPLIT = 2, PROF_CATEGORIES = 3 };
 struct ProfScope {
     int cat;
     cudaStream_t s;
@@ -160,11 +160,26 @@ struct om_matrix {
 // sweep order t in tiles of 32; per tile the entries reaching earlier tiles
 // in sliced-ELL layout (slot-major, 32 rows per slot, zero-padded) and the
 // dense inverse of the 32 x 32 diagonal block (column-major).
+// Each tile's slots come in two groups: first the "near" slots (entries in
+// the `lag` tiles just before it), then the "far" ones (older tiles), so that
+// the split sweep can hand the far sums to helper blocks in units of at most
+// kUnitSlots slots.
+struct SweepUnit {
+    int64_t off;   // entry offset of the unit's first slot
+    int32_t tile;  // tile T the unit belongs to
+    int32_t ns;    // slots in the unit
+};
 struct TilePlan {
     int64_t N = 0, ntiles = 0, padded_entries = 0;
     int64_t nchunks = 0;           // streamed chunks of 32 slots over all tiles
+    int lag = 0;                   // near band, in tiles
+    int64_t nunits = 0;            // far units over all tiles
+    int64_t near_entries = 0;      // padded near entries (streamed by the main block)
     bool forward = true;
     omss::DBuf<int64_t> tile_ptr;  // ntiles + 1 offsets into col / val
+    omss::DBuf<int32_t> near_w;    // ntiles: near slots of each tile
+    omss::DBuf<int32_t> tile_units;  // ntiles + 1: far units of tile T
+    omss::DBuf<SweepUnit> units;   // nunits
     omss::DBuf<int32_t> col;       // sweep-order column t_j
     omss::DBuf<float2> val32;      // complex64 values
     omss::DBuf<double2> val64;     // complex128 values (optional)
@@ -181,6 +196,7 @@ struct om_ilu {
     TilePlan L, U;             // forward L (unit), backward U
     TilePlan UH, LH;           // conjugate transposes: forward U^H, backward L^H (unit)
     int64_t n_guarded = 0;
+    double seconds[4] = {0, 0, 0, 0};  // host wall time: copy-out, ILUT, DAG depths, sweep layout + upload
     bool has_transpose = false;
     bool has_fp64 = false;
     cudaStream_t owner_stream = nullptr;
@@ -195,14 +211,22 @@ void spmv_c128(const int64_t *rowptr, const int32_t *col, const double2 *val, in
 void spmv_c64(const int64_t *rowptr, const int32_t *col, const float2 *val, int64_t N,
               const float2 *x, float2 *y, cudaStream_t s);
 
-// Tiled sweeps z = T^{-1} v in natural order (v and z may alias).
-void tile_sweep_c64(const TilePlan &P, const float2 *v, float2 *z, cudaStream_t s);
+// Tiled sweeps z = T^{-1} v in natural order (v and z may alias).  The
+// complex64 sweep runs split over all SMs (splitsweep.cu) when allow_split
+// is set, the plan qualifies and the calling thread has not asked for
+// single-block sweeps; otherwise one thread block sweeps.
+void tile_sweep_c64(const TilePlan &P, const float2 *v, float2 *z, cudaStream_t s, bool allow_split = true);
 void tile_sweep_c128(const TilePlan &P, const double2 *v, double2 *z, cudaStream_t s);
+bool split_sweep_c64(const TilePlan &P, const float2 *v, float2 *z, cudaStream_t s);
+// Per host thread: true makes tile_sweep_c64 use one block (used where several
+// sweeps run concurrently on one GPU, since a split sweep wants every SM).
+void set_single_block_sweeps(bool on);
 
 // z = M^{-1} v (or M^{-H} v) with complex128 vectors; fp64 selects complex128
 // sweeps, otherwise the complex64 factors are used through tmp32 (N entries).
+// allow_split = false keeps the complex64 sweeps in one block (no allocation).
 void precond_apply(const om_ilu &M, bool conj_transpose, bool fp64, const double2 *v, double2 *z,
-                   float2 *tmp32, cudaStream_t s);
+                   float2 *tmp32, cudaStream_t s, bool allow_split = true);
 void to_c64(const double2 *v, int64_t N, float2 *out, cudaStream_t s);
 void to_c128(const float2 *v, int64_t N, double2 *out, cudaStream_t s);
 

@@ -17,6 +17,7 @@
 // (tilesweep.cu): complex64 always, complex128 on request, and the
 // conjugate transposes U^H, L^H when the adjoint needs them.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <complex>
 #include <memory>
@@ -299,12 +300,16 @@ extern "C" om_status om_ilu_factor(const om_matrix *A, double droptol, double fi
         std::vector<int64_t> rp;
         std::vector<int32_t> ci;
         std::vector<double2> va;
+        using clk = std::chrono::steady_clock;
+        const auto c0 = clk::now();
         csr_to_host(*A, rp, ci, va, s);
         const int64_t N = A->N;
         HostTri L, U;
         std::vector<cd> diag;
         int64_t guarded_count = 0;
+        const auto c1 = clk::now();
         ilut_host(N, rp, ci, va, droptol, fill, (flags & 1) != 0, L, U, diag, guarded_count);
+        const auto c2 = clk::now();
         auto M = std::make_unique<om_ilu>();
         M->owner_stream = s;
         M->N = N;
@@ -313,6 +318,7 @@ extern "C" om_status om_ilu_factor(const om_matrix *A, double droptol, double fi
         M->nnz_u = (int64_t)U.ci.size() + N;
         M->levels_l = dag_depth(N, L, true);
         M->levels_u = dag_depth(N, U, false);
+        const auto c3 = clk::now();
         const bool want64 = (flags & 4) != 0;
         M->has_fp64 = want64;
         build_tile_plan(M->L, N, L.rp, L.ci, L.va, nullptr, true, want64, s);
@@ -326,7 +332,20 @@ extern "C" om_status om_ilu_factor(const om_matrix *A, double droptol, double fi
             M->has_transpose = true;
         }
         OM_CUDA_TRY(cudaStreamSynchronize(s));
+        const auto c4 = clk::now();
+        auto sec = [](clk::time_point a, clk::time_point b) { return std::chrono::duration<double>(b - a).count(); };
+        M->seconds[0] = sec(c0, c1);
+        M->seconds[1] = sec(c1, c2);
+        M->seconds[2] = sec(c2, c3);
+        M->seconds[3] = sec(c3, c4);
         *out = M.release();
+    });
+}
+
+extern "C" om_status om_ilu_timings(const om_ilu *M, double seconds[4]) {
+    return guarded([&] {
+        OM_REQUIRE(M && seconds, "om_ilu_timings: NULL argument");
+        for (int q = 0; q < 4; ++q) seconds[q] = M->seconds[q];
     });
 }
 

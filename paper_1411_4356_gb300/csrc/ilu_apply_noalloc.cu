@@ -70,7 +70,7 @@ extern "C" om_status om_ilu_apply_noalloc(const om_ilu *M, int32_t flags, const 
         cudaStream_t s = as_stream(stream);
         const DeviceScratch d = scratch_for_current_device();
         precond_apply(*M, conj_transpose, fp64, reinterpret_cast<const double2 *>(v), reinterpret_cast<double2 *>(z),
-                      d.work, s);
+                      d.work, s, /*allow_split=*/false);
         OM_CUDA_TRY(cudaStreamSynchronize(s));
     });
 }

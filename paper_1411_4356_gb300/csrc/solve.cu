@@ -216,14 +216,14 @@ extern "C" om_status om_steady_state_solve(const om_matrix *A, const om_ilu *M, 
 extern "C" om_status om_ilu_apply(const om_ilu *M, int32_t flags, const double *v, double *z, void *stream) {
     return guarded([&] {
         OM_REQUIRE(M && v && z, "om_ilu_apply: NULL argument");
-        const bool conj_transpose = (flags & 2) != 0, fp64 = (flags & 1) != 0;
+        const bool conj_transpose = (flags & 2) != 0, fp64 = (flags & 1) != 0, single = (flags & 4) != 0;
         OM_REQUIRE(!conj_transpose || M->has_transpose, "om_ilu_apply: factor built without conjugate transposes");
         OM_REQUIRE(!fp64 || M->has_fp64, "om_ilu_apply: factor built without complex128 sweep data");
         cudaStream_t s = as_stream(stream);
         DBuf<float2> tmp;
         if (!fp64) tmp.alloc(M->N, s);
         precond_apply(*M, conj_transpose, fp64, reinterpret_cast<const double2 *>(v), reinterpret_cast<double2 *>(z),
-                      tmp.p, s);
+                      tmp.p, s, !single);
         tmp.release(s);
         OM_CUDA_TRY(cudaStreamSynchronize(s));
     });

@@ -32,6 +32,7 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <memory>
 #include <thread>
 
 #include "common.cuh"
@@ -39,7 +40,9 @@
 
 namespace omss {
 using tsw::kChunkSlots;
+using tsw::kSweepLag;
 using tsw::kTile;
+using tsw::kUnitSlots;
 using tsw::kTileWarps;
 namespace {
 
@@ -68,6 +71,22 @@ using cd = std::complex<double>;
 // Builds the tiled form of a strict triangular factor T (CSR over rows r):
 // forward (lower, rows in increasing r) or backward (upper, decreasing r);
 // diag == nullptr means a unit diagonal.
+namespace {
+// Runs body(Tb, Te) over [0, n) split into contiguous ranges, one per host thread.
+template <class F>
+void parallel_ranges(int64_t n, F &&body) {
+    unsigned nt = std::max(1u, std::thread::hardware_concurrency());
+    if ((int64_t)nt > n) nt = (unsigned)std::max<int64_t>(1, n);
+    const int64_t chunk = (n + nt - 1) / nt;
+    std::vector<std::thread> pool;
+    for (unsigned q = 0; q < nt; ++q) {
+        const int64_t b = q * chunk, e = std::min(n, b + chunk);
+        if (b < e) pool.emplace_back([&body, b, e] { body(b, e); });
+    }
+    for (auto &th : pool) th.join();
+}
+}  // namespace
+
 void build_tile_plan(TilePlan &P, int64_t N, const std::vector<int64_t> &rp, const std::vector<int32_t> &ci,
                      const std::vector<cd> &va, const cd *diag, bool forward, bool want64, cudaStream_t s) {
     P.N = N;
@@ -75,29 +94,68 @@ void build_tile_plan(TilePlan &P, int64_t N, const std::vector<int64_t> &rp, con
     const int64_t ntiles = (N + kTile - 1) / kTile;
     P.ntiles = ntiles;
     auto tmap = [&](int64_t idx) { return forward ? idx : N - 1 - idx; };
-    // widths of the external (earlier-tile) part per tile
-    std::vector<int64_t> tptr(ntiles + 1, 0);
-    for (int64_t T = 0; T < ntiles; ++T) {
-        int64_t wmax = 0;
-        const int64_t t0 = T * kTile;
-        for (int64_t t = t0; t < std::min(N, t0 + kTile); ++t) {
-            const int64_t r = tmap(t);
-            int64_t cnt = 0;
-            for (int64_t q = rp[r]; q < rp[r + 1]; ++q)
-                if (tmap(ci[q]) < t0) ++cnt;
-            wmax = std::max(wmax, cnt);
+    const int lag = kSweepLag;
+    P.lag = lag;
+    // widths of the near (tiles T-lag .. T-1) and far (older) parts per tile;
+    // the near slots come first, then the far ones
+    std::vector<int32_t> nw(ntiles, 0), fw(ntiles, 0);
+    parallel_ranges(ntiles, [&](int64_t Tb, int64_t Te) {
+        for (int64_t T = Tb; T < Te; ++T) {
+            int64_t wn = 0, wf = 0;
+            const int64_t t0 = T * kTile, tnear = (T - lag) * kTile;
+            for (int64_t t = t0; t < std::min(N, t0 + kTile); ++t) {
+                const int64_t r = tmap(t);
+                int64_t cn = 0, cf = 0;
+                for (int64_t q = rp[r]; q < rp[r + 1]; ++q) {
+                    const int64_t tj = tmap(ci[q]);
+                    if (tj < t0) (tj >= tnear ? cn : cf)++;
+                }
+                wn = std::max(wn, cn);
+                wf = std::max(wf, cf);
+            }
+            nw[T] = (int32_t)wn;
+            fw[T] = (int32_t)wf;
         }
-        tptr[T + 1] = tptr[T] + wmax * kTile;
+    });
+    std::vector<int64_t> tptr(ntiles + 1, 0);
+    for (int64_t T = 0; T < ntiles; ++T) tptr[T + 1] = tptr[T] + (int64_t)(nw[T] + fw[T]) * kTile;
+    // far units: up to kUnitSlots consecutive far slots of one tile
+    std::vector<int32_t> tunits(ntiles + 1, 0);
+    std::vector<SweepUnit> units;
+    for (int64_t T = 0; T < ntiles; ++T) {
+        for (int32_t c = 0; c < fw[T]; c += kUnitSlots)
+            units.push_back(SweepUnit{tptr[T] + (int64_t)(nw[T] + c) * kTile, (int32_t)T,
+                                      std::min<int32_t>(kUnitSlots, fw[T] - c)});
+        tunits[T + 1] = (int32_t)units.size();
     }
     const int64_t total = tptr[ntiles];
-    std::vector<int32_t> scol(std::max<int64_t>(total, 1), 0);
-    std::vector<cd> sval(std::max<int64_t>(total, 1), cd(0, 0));
-    std::vector<cd> G((size_t)ntiles * kTile * kTile, cd(0, 0));
-    auto work = [&](int64_t Tb, int64_t Te) {
+    const size_t nslot = (size_t)std::max<int64_t>(total, 1);
+    const size_t ng = std::max<size_t>((size_t)ntiles * kTile * kTile, 1);
+    // staging written tile by tile by the threads (padding included), so no
+    // serial initialisation pass
+    std::unique_ptr<int32_t[]> scol(new int32_t[nslot]);
+    std::unique_ptr<float2[]> sval32(new float2[nslot]);
+    std::unique_ptr<float2[]> G32(new float2[ng]);
+    std::unique_ptr<double2[]> sval64(want64 ? new double2[nslot] : nullptr);
+    std::unique_ptr<double2[]> G64(want64 ? new double2[ng] : nullptr);
+    if (total == 0) {
+        scol[0] = 0;
+        sval32[0] = make_float2(0, 0);
+        if (want64) sval64[0] = make_double2(0, 0);
+    }
+    if (ntiles == 0) {
+        G32[0] = make_float2(0, 0);
+        if (want64) G64[0] = make_double2(0, 0);
+    }
+    parallel_ranges(ntiles, [&](int64_t Tb, int64_t Te) {
         std::vector<cd> D(kTile * kTile), Gl(kTile * kTile);
         for (int64_t T = Tb; T < Te; ++T) {
             const int64_t t0 = T * kTile;
-            const int64_t width = (tptr[T + 1] - tptr[T]) / kTile;
+            for (int64_t q = tptr[T]; q < tptr[T + 1]; ++q) {
+                scol[q] = 0;
+                sval32[q] = make_float2(0, 0);
+                if (want64) sval64[q] = make_double2(0, 0);
+            }
             std::fill(D.begin(), D.end(), cd(0, 0));
             for (int a = 0; a < kTile; ++a) {
                 const int64_t t = t0 + a;
@@ -107,19 +165,19 @@ void build_tile_plan(TilePlan &P, int64_t N, const std::vector<int64_t> &rp, con
                 }
                 const int64_t r = tmap(t);
                 D[a * kTile + a] = diag ? diag[r] : cd(1, 0);
-                int64_t k = 0;
+                int64_t kn = 0, kf = nw[T];
+                const int64_t tnear = (T - lag) * kTile;
                 for (int64_t q = rp[r]; q < rp[r + 1]; ++q) {
                     const int64_t tj = tmap(ci[q]);
                     if (tj < t0) {
-                        const int64_t idx = tptr[T] + k * kTile + a;
+                        const int64_t idx = tptr[T] + (tj >= tnear ? kn++ : kf++) * kTile + a;
                         scol[idx] = (int32_t)tj;
-                        sval[idx] = va[q];
-                        ++k;
+                        sval32[idx] = make_float2((float)va[q].real(), (float)va[q].imag());
+                        if (want64) sval64[idx] = make_double2(va[q].real(), va[q].imag());
                     } else {
                         D[a * kTile + (tj - t0)] = va[q];
                     }
                 }
-                (void)width;
             }
             // G = D^{-1} by forward substitution, column by column (FP64)
             std::fill(Gl.begin(), Gl.end(), cd(0, 0));
@@ -132,37 +190,38 @@ void build_tile_plan(TilePlan &P, int64_t N, const std::vector<int64_t> &rp, con
             }
             // column-major for the device: G[T][c][a]
             for (int c = 0; c < kTile; ++c)
-                for (int a = 0; a < kTile; ++a) G[(size_t)T * kTile * kTile + c * kTile + a] = Gl[a * kTile + c];
+                for (int a = 0; a < kTile; ++a) {
+                    const cd gv = Gl[a * kTile + c];
+                    const size_t at = (size_t)T * kTile * kTile + c * kTile + a;
+                    G32[at] = make_float2((float)gv.real(), (float)gv.imag());
+                    if (want64) G64[at] = make_double2(gv.real(), gv.imag());
+                }
         }
-    };
-    unsigned nt = std::max(1u, std::thread::hardware_concurrency());
-    if ((int64_t)nt > ntiles) nt = (unsigned)std::max<int64_t>(1, ntiles);
-    std::vector<std::thread> pool;
-    const int64_t chunk = (ntiles + nt - 1) / nt;
-    for (unsigned q = 0; q < nt; ++q) {
-        int64_t Tb = q * chunk, Te = std::min(ntiles, Tb + chunk);
-        if (Tb < Te) pool.emplace_back(work, Tb, Te);
-    }
-    for (auto &th : pool) th.join();
+    });
 
-    std::vector<float2> sval32(sval.size()), G32(G.size());
-    for (size_t q = 0; q < sval.size(); ++q) sval32[q] = make_float2((float)sval[q].real(), (float)sval[q].imag());
-    for (size_t q = 0; q < G.size(); ++q) G32[q] = make_float2((float)G[q].real(), (float)G[q].imag());
     P.tile_ptr.alloc(ntiles + 1, s);
-    P.col.alloc(scol.size(), s);
-    P.val32.alloc(sval32.size(), s);
-    P.G32.alloc(std::max<size_t>(G32.size(), 1), s);
+    P.near_w.alloc(ntiles, s);
+    P.tile_units.alloc(ntiles + 1, s);
+    P.nunits = (int64_t)units.size();
+    P.units.alloc(std::max<size_t>(units.size(), 1), s);
+    P.near_entries = 0;
+    for (int64_t T = 0; T < ntiles; ++T) P.near_entries += (int64_t)nw[T] * kTile;
+    OM_CUDA_TRY(cudaMemcpyAsync(P.near_w.p, nw.data(), sizeof(int32_t) * ntiles, cudaMemcpyHostToDevice, s));
+    OM_CUDA_TRY(cudaMemcpyAsync(P.tile_units.p, tunits.data(), sizeof(int32_t) * (ntiles + 1), cudaMemcpyHostToDevice, s));
+    if (!units.empty())
+        OM_CUDA_TRY(cudaMemcpyAsync(P.units.p, units.data(), sizeof(SweepUnit) * units.size(), cudaMemcpyHostToDevice, s));
+    P.col.alloc(nslot, s);
+    P.val32.alloc(nslot, s);
+    P.G32.alloc(ng, s);
     OM_CUDA_TRY(cudaMemcpyAsync(P.tile_ptr.p, tptr.data(), sizeof(int64_t) * (ntiles + 1), cudaMemcpyHostToDevice, s));
-    OM_CUDA_TRY(cudaMemcpyAsync(P.col.p, scol.data(), sizeof(int32_t) * scol.size(), cudaMemcpyHostToDevice, s));
-    OM_CUDA_TRY(cudaMemcpyAsync(P.val32.p, sval32.data(), sizeof(float2) * sval32.size(), cudaMemcpyHostToDevice, s));
-    if (!G32.empty())
-        OM_CUDA_TRY(cudaMemcpyAsync(P.G32.p, G32.data(), sizeof(float2) * G32.size(), cudaMemcpyHostToDevice, s));
+    OM_CUDA_TRY(cudaMemcpyAsync(P.col.p, scol.get(), sizeof(int32_t) * nslot, cudaMemcpyHostToDevice, s));
+    OM_CUDA_TRY(cudaMemcpyAsync(P.val32.p, sval32.get(), sizeof(float2) * nslot, cudaMemcpyHostToDevice, s));
+    OM_CUDA_TRY(cudaMemcpyAsync(P.G32.p, G32.get(), sizeof(float2) * ng, cudaMemcpyHostToDevice, s));
     if (want64) {
-        P.val64.alloc(sval.size(), s);
-        P.G64.alloc(std::max<size_t>(G.size(), 1), s);
-        OM_CUDA_TRY(cudaMemcpyAsync(P.val64.p, sval.data(), sizeof(double2) * sval.size(), cudaMemcpyHostToDevice, s));
-        if (!G.empty())
-            OM_CUDA_TRY(cudaMemcpyAsync(P.G64.p, G.data(), sizeof(double2) * G.size(), cudaMemcpyHostToDevice, s));
+        P.val64.alloc(nslot, s);
+        P.G64.alloc(ng, s);
+        OM_CUDA_TRY(cudaMemcpyAsync(P.val64.p, sval64.get(), sizeof(double2) * nslot, cudaMemcpyHostToDevice, s));
+        OM_CUDA_TRY(cudaMemcpyAsync(P.G64.p, G64.get(), sizeof(double2) * ng, cudaMemcpyHostToDevice, s));
     }
     P.padded_entries = total;
     P.nchunks = 0;
@@ -170,7 +229,7 @@ void build_tile_plan(TilePlan &P, int64_t N, const std::vector<int64_t> &rp, con
         const int64_t width = (tptr[T + 1] - tptr[T]) / kTile;
         P.nchunks += (width + kChunkSlots - 1) / kChunkSlots;
     }
-    OM_CUDA_TRY(cudaStreamSynchronize(s));  // host staging vectors go out of scope
+    OM_CUDA_TRY(cudaStreamSynchronize(s));  // host staging buffers go out of scope
 }
 
 __global__ void narrow(const double2 *__restrict__ v, int64_t N, float2 *__restrict__ out) {
@@ -211,7 +270,13 @@ static void launch_tile(const TilePlan &P, const CT *val, const CT *G, const CT 
     OM_CHECK_LAUNCH();
 }
 
-void tile_sweep_c64(const TilePlan &P, const float2 *v, float2 *z, cudaStream_t s) {
+namespace {
+thread_local bool tl_single_block = false;
+}
+void set_single_block_sweeps(bool on) { tl_single_block = on; }
+
+void tile_sweep_c64(const TilePlan &P, const float2 *v, float2 *z, cudaStream_t s, bool allow_split) {
+    if (allow_split && !tl_single_block && split_sweep_c64(P, v, z, s)) return;
     launch_tile<float2, 8192, 8>(P, P.val32.p, P.G32.p, v, z, s);
 }
 void tile_sweep_c128(const TilePlan &P, const double2 *v, double2 *z, cudaStream_t s) {
@@ -220,7 +285,7 @@ void tile_sweep_c128(const TilePlan &P, const double2 *v, double2 *z, cudaStream
 }
 
 void precond_apply(const om_ilu &M, bool conj_transpose, bool fp64, const double2 *v, double2 *z, float2 *tmp32,
-                   cudaStream_t s) {
+                   cudaStream_t s, bool allow_split) {
     OM_REQUIRE(!conj_transpose || M.has_transpose, "factor built without conjugate transposes");
     const TilePlan &first = conj_transpose ? M.UH : M.L;
     const TilePlan &second = conj_transpose ? M.LH : M.U;
@@ -231,8 +296,8 @@ void precond_apply(const om_ilu &M, bool conj_transpose, bool fp64, const double
         return;
     }
     to_c64(v, M.N, tmp32, s);
-    tile_sweep_c64(first, tmp32, tmp32, s);
-    tile_sweep_c64(second, tmp32, tmp32, s);
+    tile_sweep_c64(first, tmp32, tmp32, s, allow_split);
+    tile_sweep_c64(second, tmp32, tmp32, s, allow_split);
     to_c128(tmp32, M.N, z, s);
 }
 
@@ -240,6 +305,9 @@ void precond_apply(const om_ilu &M, bool conj_transpose, bool fp64, const double
 
 void TilePlan::release(cudaStream_t s) {
     tile_ptr.release(s);
+    near_w.release(s);
+    tile_units.release(s);
+    units.release(s);
     col.release(s);
     val32.release(s);
     val64.release(s);

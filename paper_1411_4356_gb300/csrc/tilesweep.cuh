@@ -78,7 +78,20 @@ __device__ inline bool wait_phase(uint64_t *bar, uint32_t parity, volatile int *
     }
 }
 
+// Waits (at most 2 s, whatever the abort flag says) for the phase of an
+// mbarrier that a copy already issued completes: producers call this before
+// they leave, so that no bulk copy into shared memory is still in flight when
+// a block that gave up exits.
+__device__ inline void drain_phase(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return;
+    const uint64_t start = now_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (now_ns() - start > 2000000000ull) return;
+}
+
 constexpr int kChunkSlots = 32;  // slots (of 32 rows) per streamed chunk
+constexpr int kSweepLag = 4;     // near band of the split sweep, in tiles
+constexpr int kUnitSlots = 16;   // slots per far unit of the split sweep
 
 
 // Shared memory of one sweep block: staged chunks, the x ring, partial sums,
@@ -136,18 +149,26 @@ __device__ void sweep_block(SweepSmem<CT, WIN, STAGES> &sm, int64_t N, int64_t n
             for (int64_t T = 0; T < ntiles && !abort_flag; ++T) {
                 const int64_t b = tile_ptr[T];
                 const int64_t width = (tile_ptr[T + 1] - b) / kTile;
+                bool stop = false;
                 for (int64_t c = 0; c < width; c += kChunkSlots, ++g) {
                     const int ns = (int)((width - c) < kChunkSlots ? (width - c) : kChunkSlots);
                     const int stage = (int)(g % STAGES);
                     const uint32_t use = (uint32_t)(g / STAGES);
-                    if (g >= STAGES && !wait_phase(&empty[stage], (use - 1) & 1, sm.abort_flag)) return;
+                    if (g >= STAGES && !wait_phase(&empty[stage], (use - 1) & 1, sm.abort_flag)) {
+                        stop = true;
+                        break;
+                    }
                     const uint32_t bc = (uint32_t)(ns * kTile * sizeof(int32_t));
                     const uint32_t bv = (uint32_t)(ns * kTile * sizeof(CT));
                     mbar_expect_tx(&full[stage], bc + bv);
                     bulk_g2s(col_s + stage * kChunkSlots * kTile, scol + b + c * kTile, bc, &full[stage]);
                     bulk_g2s(val_s + stage * kChunkSlots * kTile, sval + b + c * kTile, bv, &full[stage]);
                 }
+                if (stop) break;
             }
+            // the last STAGES chunks issued have landed before the producer leaves
+            for (int64_t q = g - 1; q >= g0 && q >= g - STAGES; --q)
+                drain_phase(&full[q % STAGES], (uint32_t)((q / STAGES) & 1));
         }
         return;
     }

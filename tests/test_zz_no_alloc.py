@@ -40,7 +40,7 @@ def test_noalloc_matches_ilu_apply(Nc, Nm, d, fill):
         ref = torch.empty(Ar.N, dtype=torch.complex128, device="cuda")
         for call_no in range(2):
             v = torch.from_numpy(rng.standard_normal(Ar.N) + 1j * rng.standard_normal(Ar.N)).cuda()
-            assert call("om_ilu_apply", M, flags, v, ref) == 0
+            assert call("om_ilu_apply", M, flags | 4, v, ref) == 0  # bit 2: one-block sweeps, as noalloc
             z = torch.full_like(v, complex("nan"))
             assert call("om_ilu_apply_noalloc", M, flags, v, z) == 0, _lib.load().om_last_error()
             torch.cuda.synchronize()
