@@ -160,10 +160,11 @@ struct om_matrix {
 // sweep order t in tiles of 32; per tile the entries reaching earlier tiles
 // in sliced-ELL layout (slot-major, 32 rows per slot, zero-padded) and the
 // dense inverse of the 32 x 32 diagonal block (column-major).
-// Each tile's slots come in two groups: first the "near" slots (entries in
-// the `lag` tiles just before it), then the "far" ones (older tiles), so that
-// the split sweep can hand the far sums to helper blocks in units of at most
-// kUnitSlots slots.
+// Each tile's slots come in three groups: the entries in the tile just
+// before it (distance 1), the "near" ones (distances 2 .. lag), and the "far"
+// ones (older tiles).  The split sweep applies the distance-1 entries as the
+// dense block H_T = G_T B_T, streams the near slots through its main block,
+// and hands the far slots to helper blocks in units of at most kUnitSlots.
 struct SweepUnit {
     int64_t off;   // entry offset of the unit's first slot
     int32_t tile;  // tile T the unit belongs to
@@ -177,7 +178,9 @@ struct TilePlan {
     int64_t near_entries = 0;      // padded near entries (streamed by the main block)
     bool forward = true;
     omss::DBuf<int64_t> tile_ptr;  // ntiles + 1 offsets into col / val
-    omss::DBuf<int32_t> near_w;    // ntiles: near slots of each tile
+    omss::DBuf<int32_t> d1_w;      // ntiles: distance-1 slots of each tile (the first group)
+    omss::DBuf<int32_t> near_w;    // ntiles: near slots of each tile (after the distance-1 ones)
+    omss::DBuf<float2> H32;        // ntiles x 32 x 32: G_T B_T, B_T the distance-1 block (column-major)
     omss::DBuf<int32_t> tile_units;  // ntiles + 1: far units of tile T
     omss::DBuf<SweepUnit> units;   // nunits
     omss::DBuf<int32_t> col;       // sweep-order column t_j

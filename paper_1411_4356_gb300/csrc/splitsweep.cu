@@ -1,35 +1,46 @@
 // Split triangular sweep (complex64): the tiled sweep of tilesweep.cu with the
 // sums over old tiles moved off the dependency chain.
 //
-// Tile T's right-hand side is v_T - E_T x_<T.  Entries of E_T whose column
-// lies in the `lag` tiles just before T ("near") need values that were
-// computed moments ago; the rest ("far") only need x of tiles < T - lag,
-// which exist long before tile T is reached.  One cooperative launch holds
+// Tile T solves D_T x_T = v_T - E_T x_<T.  The plan splits E_T by how far
+// back its columns lie: the tile just before T (distance 1), the near band
+// (distances 2 .. lag) and the far rest.  With G_T = D_T^{-1} and B_T the
+// distance-1 block,
 //
-//  * the main block (block 0), which runs the tiles in order like the
-//    single-block sweep but streams only the near slots, and takes the far
-//    sums from shared memory:
-//      warps 0-15   phase A over the near slots, then warp 0 forms
-//                   x_T = G_T (v_T - far - near) (phase B) from shared
-//                   memory only;
-//      warp 16      producer: TMA bulk copies of G_T and of the near chunks
-//                   into shared-memory rings (mbarrier full/empty pairs);
-//      warp 17      publisher: copies finished tiles from the shared window
-//                   to z, fences, and publishes the count of finished tiles;
-//      warps 18-21  gatherers: load v_T, wait until the helpers have
-//                   finished every far unit of tile T, and leave
-//                   v_T - (far sum) in a shared ring;
-//  * helper blocks, whose warps take the far units (at most 16 slots of one
-//    tile) round-robin: load the unit's columns and values, wait until the
-//    published count reaches T - lag, multiply with x from L2, write one
-//    partial per row, fence, and count the unit done for its tile.
+//     x_T = G_T (v_T - far_T - near_T) - H_T x_{T-1},   H_T = G_T B_T,
 //
-// Every wait is bounded (2 s of %globaltimer).  A wait that runs out sets
-// the block's abort flag and a global one; every other wait then returns,
-// and the rows not yet written read as NaN, which the solvers report as
-// OM_ENUMERIC.  No block waits for work that a later tile produces, and a
-// cooperative launch guarantees that all blocks are resident, so the waits
-// end whenever the hardware makes progress.
+// and only the last term depends on the tile finished just before.  One
+// cooperative launch holds
+//
+//  * the main block (block 0), which walks the tiles in order:
+//      warp 0       solver: x_T = c_T - H_T x_{T-1}, one 32 x 32
+//                   matrix-vector product on the chain;
+//      warps 1-14   workers: the near sums of tile T+1 while the solver is
+//                   on tile T (they need x only up to tile T-1);
+//      warp 15      finisher: c_T = G_T (v_T - far_T - near_T), off the
+//                   chain, as soon as the sums of tile T are in;
+//      warp 16      producer: TMA bulk copies of G_T, H_T and of the near
+//                   slots into shared-memory rings (mbarrier full/empty);
+//      warp 17      publisher: copies finished tiles to z and to the
+//                   exchange vector xs, and posts the count of finished
+//                   tiles as a hint;
+//      warps 18-25  gatherers, two teams of four taking alternate tiles:
+//                   each member sums a quarter of the far partials of the
+//                   tile, and the team leaves v_T - far_T in a shared ring;
+//  * helper blocks, whose warps take the far units (at most kUnitSlots
+//    slots of one tile) round-robin: load the unit's columns and values,
+//    follow the hint until the tiles they need are about to finish, read the
+//    x values from xs once they are there, and store one partial per row.
+//
+// Data between blocks carries its own validity: xs and the partials start as
+// an all-ones bit pattern (a NaN that no arithmetic produces) and are
+// written and read as single 64-bit words with relaxed gpu-scope accesses,
+// so a reader retries until it sees a value and no fence or counter sits on
+// the chain.  Every wait is bounded (2 s of %globaltimer); a wait that runs
+// out sets the block's abort flag and a global one, every other wait then
+// returns, and the rows not yet written read as NaN (reported by the solvers
+// as OM_ENUMERIC).  No block waits for work of a later tile, and the
+// cooperative launch keeps every block resident, so the waits end whenever
+// the hardware makes progress.
 #include <algorithm>
 
 #include "common.cuh"
@@ -39,78 +50,96 @@ namespace omss {
 using namespace tsw;
 namespace {
 
-constexpr int kConsumers = kTileWarps;           // 16
-constexpr int kProducerWarp = kConsumers;        // 16
-constexpr int kPublisherWarp = kConsumers + 1;   // 17
-constexpr int kGatherWarp0 = kConsumers + 2;     // 18..21
-constexpr int kGatherers = 4;
-constexpr int kSplitWarps = kConsumers + 2 + kGatherers;  // 22
+constexpr int kWorkers = 14;                    // warps 1..14
+constexpr int kSolverWarp = 0;
+constexpr int kFinisherWarp = kWorkers + 1;     // 15
+constexpr int kProducerWarp = kWorkers + 2;     // 16
+constexpr int kPublisherWarp = kWorkers + 3;    // 17
+constexpr int kGatherWarp0 = kWorkers + 4;      // 18..25
+constexpr int kTeam = 4;                        // gatherers per team; two teams
+constexpr int kSplitWarps = kGatherWarp0 + 2 * kTeam;  // 26
 constexpr int kSplitThreads = kSplitWarps * 32;
-constexpr int kHelperWarps = 8;                  // warps per helper block that take units
-constexpr int kWinRows = 2048;                   // shared window of recent x values
-constexpr int kStages = 8, kGStages = 8, kFarRing = 32;
+constexpr int kHelperWarps = 8;                 // warps per helper block that take units
+constexpr int kWinRows = 2048;                  // shared window of recent x values
+constexpr int kStages = 8, kGStages = 4, kFarRing = 32;
 constexpr uint64_t kWaitNs = 2000000000ull;
-static_assert(kSweepLag < kWinRows / kTile - 1, "near band must fit the window");
+constexpr unsigned long long kEmpty = ~0ull;    // "not written yet" in xs and the partials
+static_assert(kSweepLag >= 2 && kSweepLag < kWinRows / kTile - 2, "near band must fit the window");
 static_assert(kUnitSlots <= 32, "unit slots");
-static_assert(kChunkSlots == 2 * kConsumers, "phase A gives each compute warp two slots of a chunk");
+static_assert(kChunkSlots <= 3 * kWorkers, "phase A gives each worker at most three slots of a chunk");
+static_assert(kFarRing % 2 == 0, "gatherer teams alternate tiles");
 
 struct SplitArgs {
     int64_t N, ntiles;
     int forward, lag;
     const int64_t *tile_ptr;
-    const int32_t *near_w;
+    const int32_t *d1_w, *near_w;
     const int32_t *tile_units;
     const SweepUnit *units;
     int64_t nunits;
     const int32_t *scol;
     const float2 *sval;
-    const float2 *G;
+    const float2 *G, *H;
     const float2 *v;
     float2 *z;
-    float2 *far_part;  // nunits x 32
-    int *tile_cnt;     // ntiles, zero at launch
-    int *ctrl;         // [0] finished tiles published, [32] global abort; zero at launch
+    unsigned long long *xs;        // N, x in sweep order; kEmpty at launch
+    unsigned long long *far_part;  // nunits x 32; kEmpty at launch
+    int *ctrl;                     // [0] finished tiles (hint), [32] global abort; zero at launch
 };
 
 struct SplitSmem {
     int32_t *col_s;
-    float2 *val_s, *gring, *win, *part, *farsum, *ybuf;
-    uint64_t *full, *empty, *gfull, *gempty;
-    volatile int *abort_flag, *xdone, *pubdone, *maindone, *farflag;
+    float2 *val_s, *ghring, *win, *part, *farsum, *gpart, *cbuf, *ybuf;
+    uint64_t *full, *empty, *gfull, *gempty, *pfull;
+    volatile int *abort_flag, *xdone, *pubdone, *maindone, *findone, *cflag, *farflag;
     static constexpr size_t bytes() {
         return sizeof(int32_t) * kStages * kChunkSlots * kTile +
-               sizeof(float2) * (kStages * kChunkSlots * kTile + kGStages * kTile * kTile + kWinRows +
-                                 kConsumers * kTile + kFarRing * kTile + kTile) +
-               sizeof(uint64_t) * 2 * (kStages + kGStages) + sizeof(int) * (8 + kFarRing);
+               sizeof(float2) * (kStages * kChunkSlots * kTile + kGStages * 2 * kTile * kTile + kWinRows +
+                                 2 * kWorkers * kTile + kFarRing * kTile + 2 * 2 * kTeam * kTile + 2 * kTile +
+                                 2 * kTile) +
+               sizeof(uint64_t) * (2 * kStages + 2 * kGStages + 2) + sizeof(int) * (8 + kFarRing);
     }
     __device__ void carve(unsigned char *raw) {
         col_s = reinterpret_cast<int32_t *>(raw);
         val_s = reinterpret_cast<float2 *>(col_s + kStages * kChunkSlots * kTile);
-        gring = val_s + kStages * kChunkSlots * kTile;
-        win = gring + kGStages * kTile * kTile;
+        ghring = val_s + kStages * kChunkSlots * kTile;
+        win = ghring + kGStages * 2 * kTile * kTile;
         part = win + kWinRows;
-        farsum = part + kConsumers * kTile;
-        ybuf = farsum + kFarRing * kTile;
-        full = reinterpret_cast<uint64_t *>(ybuf + kTile);
+        farsum = part + 2 * kWorkers * kTile;
+        gpart = farsum + kFarRing * kTile;  // [team][tile parity][member][32]
+        cbuf = gpart + 2 * 2 * kTeam * kTile;
+        ybuf = cbuf + 2 * kTile;
+        full = reinterpret_cast<uint64_t *>(ybuf + 2 * kTile);
         empty = full + kStages;
         gfull = empty + kStages;
         gempty = gfull + kGStages;
-        int *ints = reinterpret_cast<int *>(gempty + kGStages);
+        pfull = gempty + kGStages;
+        int *ints = reinterpret_cast<int *>(pfull + 2);
         abort_flag = ints;
         xdone = ints + 1;
         pubdone = ints + 2;
         maindone = ints + 3;
+        findone = ints + 4;
+        cflag = ints + 5;
         farflag = ints + 8;
     }
 };
 
-__device__ inline int ld_acquire_gpu(const int *p) {
+__device__ inline int ld_relaxed_gpu(const int *p) {
     int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ inline void st_release_gpu(int *p, int v) {
-    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ inline void st_relaxed_gpu(int *p, int v) {
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ inline unsigned long long ld_relaxed_gpu64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ inline void st_relaxed_gpu64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ inline int ld_acquire_cta(volatile int *p) {
     int v;
@@ -119,6 +148,12 @@ __device__ inline int ld_acquire_cta(volatile int *p) {
 }
 __device__ inline void st_release_cta(volatile int *p, int v) {
     asm volatile("st.release.cta.shared.b32 [%0], %1;" ::"r"(smem_u32(const_cast<int *>(p))), "r"(v) : "memory");
+}
+__device__ inline unsigned long long pack(float2 v) {
+    return (unsigned long long)__float_as_uint(v.x) | ((unsigned long long)__float_as_uint(v.y) << 32);
+}
+__device__ inline float2 unpack(unsigned long long u) {
+    return make_float2(__uint_as_float((unsigned)(u & 0xffffffffu)), __uint_as_float((unsigned)(u >> 32)));
 }
 
 // Waits until a shared counter reaches `target`; false once the block aborts
@@ -136,21 +171,17 @@ __device__ inline bool wait_shared_ge(volatile int *flag, int target, volatile i
     }
 }
 
-// Waits until a global counter reaches `target`, polled with a pause of
-// ns_per_gap per missing count (at most ns_max) between reads; false on a
-// global or block abort or after kWaitNs.
-__device__ inline bool wait_global_ge(const int *flag, int target, int *gabort, volatile int *abort, int &seen,
-                                      int ns_per_gap, int ns_max) {
-    if (seen >= target) return true;
-    seen = ld_acquire_gpu(flag);
-    if (seen >= target) return true;
+// A bounded retry loop for the cross-block waits: `ready()` is polled with a
+// pause of `pause_ns` in between; false on a global or block abort or after
+// kWaitNs (which sets the global abort).
+template <class F>
+__device__ inline bool poll_until(F &&ready, int *gabort, volatile int *abort, unsigned pause_ns) {
+    if (ready()) return true;
     const uint64_t start = now_ns();
     for (;;) {
-        if (ld_acquire_gpu(gabort) || (abort && *abort)) return false;
-        const int gap = target - seen;
-        __nanosleep((unsigned)min(gap * ns_per_gap, ns_max));
-        seen = ld_acquire_gpu(flag);
-        if (seen >= target) return true;
+        if (ld_relaxed_gpu(gabort) || (abort && *abort)) return false;
+        __nanosleep(pause_ns);
+        if (ready()) return true;
         if (now_ns() - start > kWaitNs) {
             atomicExch(gabort, 1);
             if (abort) *abort = 1;
@@ -171,34 +202,40 @@ __device__ void main_block(const SplitArgs &a) {
         *sm.xdone = 0;
         *sm.pubdone = 0;
         *sm.maindone = 0;
+        *sm.findone = 0;
+        *sm.cflag = 0;
         for (int q = 0; q < kFarRing; ++q) sm.farflag[q] = 0;
         for (int q = 0; q < kStages; ++q) {
             mbar_init(&sm.full[q], 1);
-            mbar_init(&sm.empty[q], kConsumers);
+            mbar_init(&sm.empty[q], kWorkers);
         }
         for (int q = 0; q < kGStages; ++q) {
             mbar_init(&sm.gfull[q], 1);
-            mbar_init(&sm.gempty[q], 1);
+            mbar_init(&sm.gempty[q], 2);  // the finisher (G) and the solver (H)
         }
+        mbar_init(&sm.pfull[0], kWorkers);
+        mbar_init(&sm.pfull[1], kWorkers);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     volatile int *abort = sm.abort_flag;
     const int64_t N = a.N, ntiles = a.ntiles;
     int *gabort = a.ctrl + 32;
+    using O = TOps<float2>;
 
     if (warp == kProducerWarp) {
         if (lane != 0) return;
-        int64_t g = 0, tg = 0;  // near chunks and inverses issued
+        int64_t g = 0, tg = 0;  // near chunks and G/H pairs issued
         bool stop = false;
         for (int64_t T = 0; T < ntiles && !*abort && !stop; ++T) {
             const int gs = (int)(T % kGStages);
             if (T >= kGStages && !wait_phase(&sm.gempty[gs], (uint32_t)((T / kGStages - 1) & 1), abort)) break;
-            mbar_expect_tx(&sm.gfull[gs], kTile * kTile * sizeof(float2));
-            bulk_g2s(sm.gring + gs * kTile * kTile, a.G + T * kTile * kTile, kTile * kTile * sizeof(float2),
-                     &sm.gfull[gs]);
+            constexpr uint32_t kMat = kTile * kTile * sizeof(float2);
+            mbar_expect_tx(&sm.gfull[gs], 2 * kMat);
+            bulk_g2s(sm.ghring + gs * 2 * kTile * kTile, a.G + T * kTile * kTile, kMat, &sm.gfull[gs]);
+            bulk_g2s(sm.ghring + gs * 2 * kTile * kTile + kTile * kTile, a.H + T * kTile * kTile, kMat, &sm.gfull[gs]);
             ++tg;
-            const int64_t b = a.tile_ptr[T];
+            const int64_t b = a.tile_ptr[T] + (int64_t)a.d1_w[T] * kTile;  // the near slots
             const int wn = a.near_w[T];
             for (int c = 0; c < wn; c += kChunkSlots, ++g) {
                 const int ns = min(kChunkSlots, wn - c);
@@ -230,12 +267,15 @@ __device__ void main_block(const SplitArgs &a) {
             const int xd = ld_acquire_cta(sm.xdone);
             for (int T = done; T < xd; ++T) {
                 const int64_t t = (int64_t)T * kTile + lane;
-                if (t < N) a.z[rowof(t, N, a.forward)] = sm.win[t & (kWinRows - 1)];
+                if (t < N) {
+                    const float2 x = sm.win[t & (kWinRows - 1)];
+                    st_relaxed_gpu64(a.xs + t, pack(x));
+                    a.z[rowof(t, N, a.forward)] = x;
+                }
             }
-            __threadfence();
             __syncwarp();
             if (lane == 0) {
-                st_release_gpu(a.ctrl, xd);
+                st_relaxed_gpu(a.ctrl, xd);  // a hint: readers check the data itself
                 st_release_cta(sm.pubdone, xd);
             }
             __syncwarp();
@@ -251,105 +291,165 @@ __device__ void main_block(const SplitArgs &a) {
     }
 
     if (warp >= kGatherWarp0) {
-        int seen = 0;
-        for (int64_t T = warp - kGatherWarp0; T < ntiles; T += kGatherers) {
+        const int team = (warp - kGatherWarp0) / kTeam, member = (warp - kGatherWarp0) % kTeam;
+        for (int64_t T = team; T < ntiles; T += 2) {
             const int slot = (int)(T % kFarRing);
-            if (T >= kFarRing && !wait_shared_ge(sm.maindone, (int)(T - kFarRing + 1), abort)) return;
             const int ub = a.tile_units[T], ue = a.tile_units[T + 1];
             const int64_t t = T * kTile + lane;
             // v and z may alias: rows of tile T are written only after the
-            // main block has used this slot, so v_T is still intact here
-            float2 acc = t < N ? __ldcg(a.v + rowof(t, N, a.forward)) : make_float2(0, 0);
-            if (ue > ub) {
-                seen = 0;
-                if (!wait_global_ge(a.tile_cnt + T, ue - ub, gabort, abort, seen, 0, 32)) {
-                    *abort = 1;
-                    return;
-                }
-                int u = ub;
-                for (; u + 4 <= ue; u += 4) {
-                    float2 p[4];
+            // solver has passed it, so v_T is still intact here
+            float2 acc = (member == 0 && t < N) ? __ldcg(a.v + rowof(t, N, a.forward)) : O::zero();
+            // this member's units: ub + member, + kTeam, ...; loaded together,
+            // then re-read until none is empty
+            constexpr int kBatch = 16;
+            for (int u0 = ub + member; u0 < ue; u0 += kBatch * kTeam) {
+                const int cnt = min(kBatch, (ue - u0 + kTeam - 1) / kTeam);
+                const unsigned long long *src = a.far_part + (int64_t)u0 * kTile + lane;
+                unsigned long long w[kBatch];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) p[k] = __ldcg(a.far_part + (int64_t)(u + k) * kTile + lane);
-                    acc.x -= (p[0].x + p[1].x) + (p[2].x + p[3].x);
-                    acc.y -= (p[0].y + p[1].y) + (p[2].y + p[3].y);
+                for (int k = 0; k < kBatch; ++k) w[k] = k < cnt ? ld_relaxed_gpu64(src + k * kTeam * kTile) : 0ull;
+                auto there = [&] {
+                    bool ok = true;
+#pragma unroll
+                    for (int k = 0; k < kBatch; ++k) {
+                        if (k < cnt && w[k] == kEmpty) w[k] = ld_relaxed_gpu64(src + k * kTeam * kTile);
+                        ok = ok && w[k] != kEmpty;
+                    }
+                    return __all_sync(0xffffffffu, ok);
+                };
+                if (!poll_until(there, gabort, abort, 32)) {
+                    *abort = 1;
+                    break;
                 }
-                for (; u < ue; ++u) {
-                    const float2 p = __ldcg(a.far_part + (int64_t)u * kTile + lane);
-                    acc.x -= p.x;
-                    acc.y -= p.y;
+#pragma unroll
+                for (int k = 0; k < kBatch; ++k) {
+                    if (k < cnt) {
+                        const float2 p = unpack(w[k]);
+                        acc.x -= p.x;
+                        acc.y -= p.y;
+                    }
                 }
             }
-            sm.farsum[slot * kTile + lane] = acc;
-            __syncwarp();
-            if (lane == 0) st_release_cta(&sm.farflag[slot], (int)(T + 1));
+            float2 *gp = sm.gpart + ((team * 2 + ((T >> 1) & 1)) * kTeam) * kTile;
+            gp[member * kTile + lane] = acc;
+            asm volatile("bar.sync %0, %1;" ::"r"(2 + team), "n"(kTeam * 32) : "memory");
+            if (member == 0) {
+                // farsum[slot] is free once the finisher has read tile T - kFarRing
+                if (T >= kFarRing) wait_shared_ge(sm.findone, (int)(T - kFarRing + 1), abort);
+                float2 f = gp[lane];
+#pragma unroll
+                for (int k = 1; k < kTeam; ++k) f = O::add(f, gp[k * kTile + lane]);
+                sm.farsum[slot * kTile + lane] = f;
+                __syncwarp();
+                if (lane == 0) st_release_cta(&sm.farflag[slot], (int)(T + 1));
+            }
         }
         return;
     }
 
-    // ---- compute warps
-    using O = TOps<float2>;
-    int64_t g = 0;
-    for (int64_t T = 0; T < ntiles; ++T) {
-        const int64_t t0 = T * kTile;
-        const int wn = a.near_w[T];
-        // phase A: each warp takes slots warp and warp + 16 of every chunk
-        float2 acc0 = O::zero(), acc1 = O::zero();
-        bool ok = true;
-        for (int c = 0; c < wn; c += kChunkSlots, ++g) {
-            const int ns = min(kChunkSlots, wn - c);
-            const int stage = (int)(g % kStages);
-            if (!wait_phase(&sm.full[stage], (uint32_t)((g / kStages) & 1), abort)) ok = false;
-            if (ok) {
-                const int32_t *cs = sm.col_s + stage * kChunkSlots * kTile;
-                const float2 *vs = sm.val_s + stage * kChunkSlots * kTile;
-                const int q0 = warp, q1 = warp + kConsumers;
-                const int32_t j0 = q0 < ns ? cs[q0 * kTile + lane] : 0;
-                const int32_t j1 = q1 < ns ? cs[q1 * kTile + lane] : 0;
-                const float2 a0 = q0 < ns ? vs[q0 * kTile + lane] : O::zero();
-                const float2 a1 = q1 < ns ? vs[q1 * kTile + lane] : O::zero();
-                acc0 = O::fma(a0, sm.win[j0 & (kWinRows - 1)], acc0);
-                acc1 = O::fma(a1, sm.win[j1 & (kWinRows - 1)], acc1);
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&sm.empty[stage]);
-        }
-        sm.part[warp * kTile + lane] = O::add(acc0, acc1);
-        consumer_barrier();
-        if (warp == 0) {
-            // phase B: y = (v_T - far sum) - near sums; x_T = G_T y
-            const int64_t t = t0 + lane;
+    if (warp == kFinisherWarp) {
+        // c_T = G_T (v_T - far_T - near_T) into cbuf[T % 2]
+        for (int64_t T = 0; T < ntiles; ++T) {
+            const int64_t t = T * kTile + lane;
             const int slot = (int)(T % kFarRing);
+            const int gs = (int)(T % kGStages);
+            const bool fr = wait_shared_ge(&sm.farflag[slot], (int)(T + 1), abort);
+            wait_phase(&sm.gfull[gs], (uint32_t)((T / kGStages) & 1), abort);
+            wait_phase(&sm.pfull[T & 1], (uint32_t)((T >> 1) & 1), abort);
             float2 y = O::zero();
-            if (wait_shared_ge(&sm.farflag[slot], (int)(T + 1), abort) && t < N) {
+            if (fr && t < N) {
                 float2 s4[4] = {O::zero(), O::zero(), O::zero(), O::zero()};
+                const float2 *pt = sm.part + (T & 1) * kWorkers * kTile;
 #pragma unroll
-                for (int w = 0; w < kConsumers; ++w) s4[w & 3] = O::add(s4[w & 3], sm.part[w * kTile + lane]);
+                for (int w = 0; w < kWorkers; ++w) s4[w & 3] = O::add(s4[w & 3], pt[w * kTile + lane]);
                 y = O::sub(sm.farsum[slot * kTile + lane], O::add(O::add(s4[0], s4[1]), O::add(s4[2], s4[3])));
             }
-            sm.ybuf[lane] = y;
-            const int gs = (int)(T % kGStages);
-            wait_phase(&sm.gfull[gs], (uint32_t)((T / kGStages) & 1), abort);
             __syncwarp();
-            const float2 *G = sm.gring + gs * kTile * kTile;
+            if (lane == 0) st_release_cta(sm.findone, (int)(T + 1));
+            sm.ybuf[lane] = y;
+            __syncwarp();
+            const float2 *G = sm.ghring + gs * 2 * kTile * kTile;
             float2 x4[4] = {O::zero(), O::zero(), O::zero(), O::zero()};
 #pragma unroll
             for (int c = 0; c < kTile; ++c) x4[c & 3] = O::fma(G[c * kTile + lane], sm.ybuf[c], x4[c & 3]);
-            float2 x = O::add(O::add(x4[0], x4[1]), O::add(x4[2], x4[3]));
+            // cbuf[T % 2] is free once the solver has used c_{T-2}
+            if (T >= 2) wait_shared_ge(sm.maindone, (int)(T - 1), abort);
+            sm.cbuf[(T & 1) * kTile + lane] = O::add(O::add(x4[0], x4[1]), O::add(x4[2], x4[3]));
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive(&sm.gempty[gs]);
-                st_release_cta(sm.maindone, (int)(T + 1));
+                st_release_cta(sm.cflag, (int)(T + 1));
             }
-            // tile T reuses the window rows of tile T - kWinRows/32: published by now?
-            const int64_t need_pub = T + 1 - (kWinRows / kTile - 1);
-            if (need_pub > 0) wait_shared_ge(sm.pubdone, (int)need_pub, abort);
-            if (*abort) x.x = x.y = __int_as_float(0x7fc00000);
-            if (t < N) sm.win[t & (kWinRows - 1)] = x;
-            __syncwarp();
-            if (lane == 0) st_release_cta(sm.xdone, (int)(T + 1));
         }
-        consumer_barrier();
+        return;
+    }
+
+    if (warp != kSolverWarp) {
+        // ---- workers: near sums of tile T into part[T % 2]
+        const int wk = warp - 1;
+        int64_t g = 0;
+        for (int64_t T = 0; T < ntiles; ++T) {
+            // x up to tile T-2 is in the window and part[T % 2] is free again
+            wait_shared_ge(sm.xdone, (int)(T - 1), abort);
+            const int wn = a.near_w[T];
+            float2 acc0 = O::zero(), acc1 = O::zero(), acc2 = O::zero();
+            bool ok = true;
+            for (int c = 0; c < wn; c += kChunkSlots, ++g) {
+                const int ns = min(kChunkSlots, wn - c);
+                const int stage = (int)(g % kStages);
+                if (!wait_phase(&sm.full[stage], (uint32_t)((g / kStages) & 1), abort)) ok = false;
+                if (ok) {
+                    const int32_t *cs = sm.col_s + stage * kChunkSlots * kTile;
+                    const float2 *vs = sm.val_s + stage * kChunkSlots * kTile;
+                    const int q0 = wk, q1 = wk + kWorkers, q2 = wk + 2 * kWorkers;
+                    const int32_t j0 = q0 < ns ? cs[q0 * kTile + lane] : 0;
+                    const int32_t j1 = q1 < ns ? cs[q1 * kTile + lane] : 0;
+                    const int32_t j2 = q2 < ns ? cs[q2 * kTile + lane] : 0;
+                    const float2 a0 = q0 < ns ? vs[q0 * kTile + lane] : O::zero();
+                    const float2 a1 = q1 < ns ? vs[q1 * kTile + lane] : O::zero();
+                    const float2 a2 = q2 < ns ? vs[q2 * kTile + lane] : O::zero();
+                    acc0 = O::fma(a0, sm.win[j0 & (kWinRows - 1)], acc0);
+                    acc1 = O::fma(a1, sm.win[j1 & (kWinRows - 1)], acc1);
+                    acc2 = O::fma(a2, sm.win[j2 & (kWinRows - 1)], acc2);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm.empty[stage]);
+            }
+            sm.part[((T & 1) * kWorkers + wk) * kTile + lane] = O::add(O::add(acc0, acc1), acc2);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.pfull[T & 1]);
+        }
+        return;
+    }
+
+    // ---- solver (warp 0): x_T = c_T - H_T x_{T-1}
+    float2 xprev = O::zero();
+    for (int64_t T = 0; T < ntiles; ++T) {
+        const int64_t t = T * kTile + lane;
+        const int gs = (int)(T % kGStages);
+        sm.ybuf[kTile + lane] = xprev;
+        wait_phase(&sm.gfull[gs], (uint32_t)((T / kGStages) & 1), abort);
+        wait_shared_ge(sm.cflag, (int)(T + 1), abort);
+        __syncwarp();
+        const float2 *Hm = sm.ghring + gs * 2 * kTile * kTile + kTile * kTile;
+        float2 h4[4] = {O::zero(), O::zero(), O::zero(), O::zero()};
+#pragma unroll
+        for (int c = 0; c < kTile; ++c) h4[c & 3] = O::fma(Hm[c * kTile + lane], sm.ybuf[kTile + c], h4[c & 3]);
+        float2 x = O::sub(sm.cbuf[(T & 1) * kTile + lane], O::add(O::add(h4[0], h4[1]), O::add(h4[2], h4[3])));
+        __syncwarp();
+        if (lane == 0) {
+            mbar_arrive(&sm.gempty[gs]);
+            st_release_cta(sm.maindone, (int)(T + 1));
+        }
+        // tile T reuses the window rows of tile T - kWinRows/32: published by now?
+        const int64_t need_pub = T + 1 - (kWinRows / kTile - 1);
+        if (need_pub > 0) wait_shared_ge(sm.pubdone, (int)need_pub, abort);
+        if (*abort) x.x = x.y = __int_as_float(0x7fc00000);
+        if (t >= N) x = O::zero();
+        sm.win[t & (kWinRows - 1)] = x;
+        xprev = x;
+        __syncwarp();
+        if (lane == 0) st_release_cta(sm.xdone, (int)(T + 1));
     }
 }
 
@@ -374,20 +474,30 @@ __device__ void helper_block(const SplitArgs &a) {
                 val[q] = make_float2(0, 0);
             }
         }
-        const int need = U.tile - a.lag;  // tiles < T - lag must be finished
-        if (!wait_global_ge(a.ctrl, need, gabort, nullptr, seen, 128, 8192)) return;
+        // x of tiles < T - lag: follow the hint until those tiles are about
+        // to finish, then poll the values themselves
+        const int need = U.tile - a.lag - 2;
+        if (seen < need) {
+            const unsigned pause = (unsigned)min((need - seen) * 128, 8192);
+            if (!poll_until([&] { return (seen = ld_relaxed_gpu(a.ctrl)) >= need; }, gabort, nullptr, pause)) return;
+        }
+        unsigned long long xw[kUnitSlots];
+#pragma unroll
+        for (int q = 0; q < kUnitSlots; ++q) xw[q] = q < U.ns ? ld_relaxed_gpu64(a.xs + col[q]) : 0ull;
+        auto all_there = [&] {
+            bool ok = true;
+#pragma unroll
+            for (int q = 0; q < kUnitSlots; ++q) {
+                if (xw[q] == kEmpty) xw[q] = ld_relaxed_gpu64(a.xs + col[q]);
+                ok = ok && xw[q] != kEmpty;
+            }
+            return __all_sync(0xffffffffu, ok);
+        };
+        if (!poll_until(all_there, gabort, nullptr, 64)) return;
         float2 acc = make_float2(0, 0);
 #pragma unroll
-        for (int q = 0; q < kUnitSlots; ++q) {
-            if (q < U.ns) {
-                const float2 xj = __ldcg(a.z + rowof(col[q], a.N, a.forward));
-                acc = TOps<float2>::fma(val[q], xj, acc);
-            }
-        }
-        a.far_part[u * kTile + lane] = acc;
-        __threadfence();
-        __syncwarp();
-        if (lane == 0) atomicAdd(a.tile_cnt + U.tile, 1);
+        for (int q = 0; q < kUnitSlots; ++q) acc = TOps<float2>::fma(val[q], unpack(xw[q]), acc);
+        st_relaxed_gpu64(a.far_part + u * kTile + lane, pack(acc));
     }
 }
 
@@ -414,13 +524,15 @@ bool split_sweep_c64(const TilePlan &P, const float2 *v, float2 *z, cudaStream_t
     }
     if (!coop || blocks_per_sm < 1) return false;
     const int64_t max_blocks = (int64_t)num_sms() * blocks_per_sm;
-    const int64_t helpers = std::max<int64_t>(1, std::min<int64_t>(max_blocks - 1, (P.nunits + kHelperWarps - 1) / kHelperWarps));
-    DBuf<float2> part;
-    DBuf<int> cnt, ctrl;
+    const int64_t helpers =
+        std::max<int64_t>(1, std::min<int64_t>(max_blocks - 1, (P.nunits + kHelperWarps - 1) / kHelperWarps));
+    DBuf<unsigned long long> part, xs;
+    DBuf<int> ctrl;
     part.alloc((size_t)P.nunits * kTile, s);
-    cnt.alloc(P.ntiles, s);
+    xs.alloc((size_t)P.N, s);
     ctrl.alloc(64, s);
-    OM_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(int) * P.ntiles, s));
+    OM_CUDA_TRY(cudaMemsetAsync(part.p, 0xff, sizeof(unsigned long long) * P.nunits * kTile, s));
+    OM_CUDA_TRY(cudaMemsetAsync(xs.p, 0xff, sizeof(unsigned long long) * P.N, s));
     OM_CUDA_TRY(cudaMemsetAsync(ctrl.p, 0, sizeof(int) * 64, s));
     SplitArgs a;
     a.N = P.N;
@@ -428,6 +540,7 @@ bool split_sweep_c64(const TilePlan &P, const float2 *v, float2 *z, cudaStream_t
     a.forward = P.forward ? 1 : 0;
     a.lag = P.lag;
     a.tile_ptr = P.tile_ptr.p;
+    a.d1_w = P.d1_w.p;
     a.near_w = P.near_w.p;
     a.tile_units = P.tile_units.p;
     a.units = P.units.p;
@@ -435,10 +548,11 @@ bool split_sweep_c64(const TilePlan &P, const float2 *v, float2 *z, cudaStream_t
     a.scol = P.col.p;
     a.sval = P.val32.p;
     a.G = P.G32.p;
+    a.H = P.H32.p;
     a.v = v;
     a.z = z;
+    a.xs = xs.p;
     a.far_part = part.p;
-    a.tile_cnt = cnt.p;
     a.ctrl = ctrl.p;
     void *args[] = {&a};
     {
@@ -448,7 +562,7 @@ bool split_sweep_c64(const TilePlan &P, const float2 *v, float2 *z, cudaStream_t
         omss::note_launch();
     }
     part.release(s);
-    cnt.release(s);
+    xs.release(s);
     ctrl.release(s);
     return true;
 }

@@ -96,35 +96,36 @@ void build_tile_plan(TilePlan &P, int64_t N, const std::vector<int64_t> &rp, con
     auto tmap = [&](int64_t idx) { return forward ? idx : N - 1 - idx; };
     const int lag = kSweepLag;
     P.lag = lag;
-    // widths of the near (tiles T-lag .. T-1) and far (older) parts per tile;
-    // the near slots come first, then the far ones
-    std::vector<int32_t> nw(ntiles, 0), fw(ntiles, 0);
+    // widths of the distance-1 (tile T-1), near (tiles T-lag .. T-2) and far
+    // (older) groups of slots per tile, stored in that order
+    std::vector<int32_t> w1(ntiles, 0), nw(ntiles, 0), fw(ntiles, 0);
+    auto group = [&](int64_t tj, int64_t t0) { return tj >= t0 - kTile ? 0 : (tj >= t0 - (int64_t)lag * kTile ? 1 : 2); };
     parallel_ranges(ntiles, [&](int64_t Tb, int64_t Te) {
         for (int64_t T = Tb; T < Te; ++T) {
-            int64_t wn = 0, wf = 0;
-            const int64_t t0 = T * kTile, tnear = (T - lag) * kTile;
+            int64_t wmax[3] = {0, 0, 0};
+            const int64_t t0 = T * kTile;
             for (int64_t t = t0; t < std::min(N, t0 + kTile); ++t) {
                 const int64_t r = tmap(t);
-                int64_t cn = 0, cf = 0;
+                int64_t cnt[3] = {0, 0, 0};
                 for (int64_t q = rp[r]; q < rp[r + 1]; ++q) {
                     const int64_t tj = tmap(ci[q]);
-                    if (tj < t0) (tj >= tnear ? cn : cf)++;
+                    if (tj < t0) cnt[group(tj, t0)]++;
                 }
-                wn = std::max(wn, cn);
-                wf = std::max(wf, cf);
+                for (int k = 0; k < 3; ++k) wmax[k] = std::max(wmax[k], cnt[k]);
             }
-            nw[T] = (int32_t)wn;
-            fw[T] = (int32_t)wf;
+            w1[T] = (int32_t)wmax[0];
+            nw[T] = (int32_t)wmax[1];
+            fw[T] = (int32_t)wmax[2];
         }
     });
     std::vector<int64_t> tptr(ntiles + 1, 0);
-    for (int64_t T = 0; T < ntiles; ++T) tptr[T + 1] = tptr[T] + (int64_t)(nw[T] + fw[T]) * kTile;
+    for (int64_t T = 0; T < ntiles; ++T) tptr[T + 1] = tptr[T] + (int64_t)(w1[T] + nw[T] + fw[T]) * kTile;
     // far units: up to kUnitSlots consecutive far slots of one tile
     std::vector<int32_t> tunits(ntiles + 1, 0);
     std::vector<SweepUnit> units;
     for (int64_t T = 0; T < ntiles; ++T) {
         for (int32_t c = 0; c < fw[T]; c += kUnitSlots)
-            units.push_back(SweepUnit{tptr[T] + (int64_t)(nw[T] + c) * kTile, (int32_t)T,
+            units.push_back(SweepUnit{tptr[T] + (int64_t)(w1[T] + nw[T] + c) * kTile, (int32_t)T,
                                       std::min<int32_t>(kUnitSlots, fw[T] - c)});
         tunits[T + 1] = (int32_t)units.size();
     }
@@ -136,6 +137,7 @@ void build_tile_plan(TilePlan &P, int64_t N, const std::vector<int64_t> &rp, con
     std::unique_ptr<int32_t[]> scol(new int32_t[nslot]);
     std::unique_ptr<float2[]> sval32(new float2[nslot]);
     std::unique_ptr<float2[]> G32(new float2[ng]);
+    std::unique_ptr<float2[]> H32(new float2[ng]);
     std::unique_ptr<double2[]> sval64(want64 ? new double2[nslot] : nullptr);
     std::unique_ptr<double2[]> G64(want64 ? new double2[ng] : nullptr);
     if (total == 0) {
@@ -145,10 +147,11 @@ void build_tile_plan(TilePlan &P, int64_t N, const std::vector<int64_t> &rp, con
     }
     if (ntiles == 0) {
         G32[0] = make_float2(0, 0);
+        H32[0] = make_float2(0, 0);
         if (want64) G64[0] = make_double2(0, 0);
     }
     parallel_ranges(ntiles, [&](int64_t Tb, int64_t Te) {
-        std::vector<cd> D(kTile * kTile), Gl(kTile * kTile);
+        std::vector<cd> D(kTile * kTile), Gl(kTile * kTile), B(kTile * kTile);
         for (int64_t T = Tb; T < Te; ++T) {
             const int64_t t0 = T * kTile;
             for (int64_t q = tptr[T]; q < tptr[T + 1]; ++q) {
@@ -157,6 +160,7 @@ void build_tile_plan(TilePlan &P, int64_t N, const std::vector<int64_t> &rp, con
                 if (want64) sval64[q] = make_double2(0, 0);
             }
             std::fill(D.begin(), D.end(), cd(0, 0));
+            std::fill(B.begin(), B.end(), cd(0, 0));
             for (int a = 0; a < kTile; ++a) {
                 const int64_t t = t0 + a;
                 if (t >= N) {
@@ -165,12 +169,13 @@ void build_tile_plan(TilePlan &P, int64_t N, const std::vector<int64_t> &rp, con
                 }
                 const int64_t r = tmap(t);
                 D[a * kTile + a] = diag ? diag[r] : cd(1, 0);
-                int64_t kn = 0, kf = nw[T];
-                const int64_t tnear = (T - lag) * kTile;
+                int64_t k[3] = {0, w1[T], w1[T] + nw[T]};
                 for (int64_t q = rp[r]; q < rp[r + 1]; ++q) {
                     const int64_t tj = tmap(ci[q]);
                     if (tj < t0) {
-                        const int64_t idx = tptr[T] + (tj >= tnear ? kn++ : kf++) * kTile + a;
+                        const int gr = group(tj, t0);
+                        if (gr == 0) B[a * kTile + (tj - (t0 - kTile))] = va[q];
+                        const int64_t idx = tptr[T] + (k[gr]++) * kTile + a;
                         scol[idx] = (int32_t)tj;
                         sval32[idx] = make_float2((float)va[q].real(), (float)va[q].imag());
                         if (want64) sval64[idx] = make_double2(va[q].real(), va[q].imag());
@@ -188,25 +193,32 @@ void build_tile_plan(TilePlan &P, int64_t N, const std::vector<int64_t> &rp, con
                     Gl[a * kTile + c] = sacc / D[a * kTile + a];
                 }
             }
-            // column-major for the device: G[T][c][a]
+            // column-major for the device: G[T][c][a], and H = G B likewise
             for (int c = 0; c < kTile; ++c)
                 for (int a = 0; a < kTile; ++a) {
                     const cd gv = Gl[a * kTile + c];
+                    cd hv(0, 0);
+                    for (int b = 0; b < kTile; ++b) hv += Gl[a * kTile + b] * B[b * kTile + c];
                     const size_t at = (size_t)T * kTile * kTile + c * kTile + a;
                     G32[at] = make_float2((float)gv.real(), (float)gv.imag());
+                    H32[at] = make_float2((float)hv.real(), (float)hv.imag());
                     if (want64) G64[at] = make_double2(gv.real(), gv.imag());
                 }
         }
     });
 
     P.tile_ptr.alloc(ntiles + 1, s);
+    P.d1_w.alloc(ntiles, s);
     P.near_w.alloc(ntiles, s);
     P.tile_units.alloc(ntiles + 1, s);
+    P.H32.alloc(ng, s);
     P.nunits = (int64_t)units.size();
     P.units.alloc(std::max<size_t>(units.size(), 1), s);
     P.near_entries = 0;
     for (int64_t T = 0; T < ntiles; ++T) P.near_entries += (int64_t)nw[T] * kTile;
+    OM_CUDA_TRY(cudaMemcpyAsync(P.d1_w.p, w1.data(), sizeof(int32_t) * ntiles, cudaMemcpyHostToDevice, s));
     OM_CUDA_TRY(cudaMemcpyAsync(P.near_w.p, nw.data(), sizeof(int32_t) * ntiles, cudaMemcpyHostToDevice, s));
+    OM_CUDA_TRY(cudaMemcpyAsync(P.H32.p, H32.get(), sizeof(float2) * ng, cudaMemcpyHostToDevice, s));
     OM_CUDA_TRY(cudaMemcpyAsync(P.tile_units.p, tunits.data(), sizeof(int32_t) * (ntiles + 1), cudaMemcpyHostToDevice, s));
     if (!units.empty())
         OM_CUDA_TRY(cudaMemcpyAsync(P.units.p, units.data(), sizeof(SweepUnit) * units.size(), cudaMemcpyHostToDevice, s));
@@ -305,7 +317,9 @@ void precond_apply(const om_ilu &M, bool conj_transpose, bool fp64, const double
 
 void TilePlan::release(cudaStream_t s) {
     tile_ptr.release(s);
+    d1_w.release(s);
     near_w.release(s);
+    H32.release(s);
     tile_units.release(s);
     units.release(s);
     col.release(s);

@@ -91,7 +91,7 @@ __device__ inline void drain_phase(uint64_t *bar, uint32_t parity) {
 
 constexpr int kChunkSlots = 32;  // slots (of 32 rows) per streamed chunk
 constexpr int kSweepLag = 4;     // near band of the split sweep, in tiles
-constexpr int kUnitSlots = 16;   // slots per far unit of the split sweep
+constexpr int kUnitSlots = 8;    // slots per far unit of the split sweep
 
 
 // Shared memory of one sweep block: staged chunks, the x ring, partial sums,
