@@ -164,13 +164,17 @@ def run_omss(args):
     rho_host = torch.empty(n * n, dtype=torch.complex128, pin_memory=True)
     stream = torch.cuda.current_stream()
 
-    def step(readback: bool, precision: int = w.precision):
+    extra = {}
+
+    def step(readback: bool, precision: int = w.precision, condest: bool = False):
         h0 = time.perf_counter()
         A = api.build_liouvillian(p, w.trace_mode, w.nth_floor)
         Ar, perm = api.permute(A)
         A.free()
         h1 = time.perf_counter()
         M = api.ilu_factor(Ar, w.droptol, w.fill)
+        if condest:  # outside the timed steps
+            extra["condest"] = api.ilu_condest(M)
         _, info = api.steady_state_solve(Ar, M, perm, restart=w.restart, tol=w.tol, precision=precision,
                                          rho_out=rho_dev)
         obs = api.observables(p.Nc, p.Nm, rho_dev)
@@ -183,8 +187,8 @@ def run_omss(args):
         Ar.free()
         return stats
 
-    for _ in range(args.warmup):
-        step(False)
+    for k in range(args.warmup):
+        step(False, condest=(k == args.warmup - 1))
     torch.cuda.synchronize()
 
     def barrier():
@@ -308,6 +312,7 @@ def run_omss(args):
                     **{"ilu_" + k: sum(st["ilu_s"][k] for st in stats) / len(stats) for k in stats[0]["ilu_s"]}},
         "iterations": its,
         "eta": s0["eta"],
+        "ilu_condest": extra.get("condest"),
         "fill": s0["fill"],
         "spmv": {"avg_launch_us": spmv_ms / max(spmv_n, 1) * 1e3, "launches": spmv_n},
         "observables": {"n_a": s0["obs"][0], "n_b": s0["obs"][1]},

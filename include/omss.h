@@ -214,6 +214,12 @@ om_status om_spmv(const om_matrix *A, const double *x, double *y, void *stream);
  * scratch from the stream-ordered allocator.  Errors: OM_EINVAL, OM_ECUDA. */
 om_status om_ilu_apply(const om_ilu *M, int32_t flags, const double *v, double *z,
                        void *stream);
+/* Sec. IV's estimate of how the preconditioner amplifies errors, read as
+ * ||(L U)^{-1} e||_inf with e the vector of ones (one forward and one
+ * backward sweep).  flags as for om_ilu_apply (bit 0: complex128 sweeps; bit
+ * 2: one-block sweeps; bit 1 is ignored).  out: HOST double.  A NaN or Inf
+ * result marks an unstable factorisation.  Errors: OM_EINVAL, OM_ECUDA. */
+om_status om_ilu_condest(const om_ilu *M, int32_t flags, double *out, void *stream);
 /* Allocation-free variant of om_ilu_apply.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory --
  * code whose device memory belongs to another allocator (a framework's

@@ -54,6 +54,7 @@ SIGNATURES = {
     "om_spmv": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
     "om_ilu_apply": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp]),
     "om_ilu_apply_noalloc": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp]),
+    "om_ilu_condest": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_dbl), c_vp]),
     "om_observables": (c_i32, [c_i32, c_i32, c_vp, ctypes.POINTER(c_dbl * 2), c_vp]),
     "om_kernel_launches": (c_i64, []),
     "om_profile": (c_i32, [c_i32]),

@@ -217,6 +217,15 @@ def ilu_apply(M: ILU, v: torch.Tensor, conj_transpose: bool = False, fp64: bool 
     return z
 
 
+def ilu_condest(M: ILU, fp64: bool = False, single_block: bool = False, stream=None) -> float:
+    """||(L U)^{-1} e||_inf, e = ones (Sec. IV's stability estimate of the factors)."""
+    out = ctypes.c_double()
+    flags = (1 if fp64 else 0) | (4 if single_block else 0)
+    check(_lib.load().om_ilu_condest(M.handle, flags, ctypes.byref(out), ctypes.c_void_p(_stream(stream))),
+          "om_ilu_condest")
+    return out.value
+
+
 def observables(Nc: int, Nm: int, rho: torch.Tensor, stream=None):
     """(<a^dag a>, <b^dag b>) of a CUDA rho."""
     flat = rho.t().contiguous().view(-1) if rho.dim() == 2 else rho

@@ -7,6 +7,7 @@
 // evaluated in FP64 at the end of every cycle; then x is divided by its
 // trace (Tr rho = 1) and scattered back to natural order, giving the
 // column-stacked rho of Eq. 4.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 
@@ -89,6 +90,28 @@ struct ForwardOps : KrylovOps<double2> {
         precond_apply(*M, false, fp64_precond, v, out, tmp32, s);
     }
 };
+
+__global__ void fill_ones(double2 *e, int64_t N) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) e[i] = make_double2(1, 0);
+}
+
+// out[0] = max_i |z_i| in one block (fixed order); +Inf if any entry is NaN or Inf
+__global__ void max_abs(const double2 *z, int64_t N, double *out) {
+    __shared__ double red[256];
+    double m = 0;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+        const double a = sqrt(cabs2(z[i]));
+        m = isfinite(a) ? fmax(m, a) : INFINITY;
+    }
+    red[threadIdx.x] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int q = 0; q < (int)blockDim.x; ++q) t = fmax(t, red[q]);
+        out[0] = t;
+    }
+}
 
 }  // namespace
 
@@ -226,6 +249,34 @@ extern "C" om_status om_ilu_apply(const om_ilu *M, int32_t flags, const double *
                       tmp.p, s, !single);
         tmp.release(s);
         OM_CUDA_TRY(cudaStreamSynchronize(s));
+    });
+}
+
+extern "C" om_status om_ilu_condest(const om_ilu *M, int32_t flags, double *out, void *stream) {
+    return guarded([&] {
+        OM_REQUIRE(M && out, "om_ilu_condest: NULL argument");
+        const bool fp64 = (flags & 1) != 0, single = (flags & 4) != 0;
+        OM_REQUIRE(!fp64 || M->has_fp64, "om_ilu_condest: factor built without complex128 sweep data");
+        cudaStream_t s = as_stream(stream);
+        DBuf<double2> e;
+        DBuf<float2> tmp;
+        DBuf<double> d;
+        e.alloc(std::max<int64_t>(M->N, 1), s);
+        d.alloc(1, s);
+        if (!fp64) tmp.alloc(std::max<int64_t>(M->N, 1), s);
+        const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((M->N + 255) / 256, 4 * num_sms()));
+        fill_ones<<<blocks, 256, 0, s>>>(e.p, M->N);
+        omss::note_launch();
+        OM_CHECK_LAUNCH();
+        precond_apply(*M, false, fp64, e.p, e.p, tmp.p, s, !single);
+        max_abs<<<1, 256, 0, s>>>(e.p, M->N, d.p);
+        omss::note_launch();
+        OM_CHECK_LAUNCH();
+        OM_CUDA_TRY(cudaMemcpyAsync(out, d.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+        OM_CUDA_TRY(cudaStreamSynchronize(s));
+        e.release(s);
+        tmp.release(s);
+        d.release(s);
     });
 }
 

@@ -122,6 +122,32 @@ def test_ilu_apply_matches_oracle(Nc, Nm, d, fill):
         assert np.abs(z32 - ref).max() <= 1e-3 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("Nc,Nm,d,fill", [(4, 10, 1e-4, 10.0), (6, 20, 1e-4, 20.0)])
+def test_ilu_condest_matches_oracle(Nc, Nm, d, fill):
+    """||(LU)^{-1} e||_inf (Sec. IV) against the oracle's factor solves."""
+    p = SystemParams(Nc, Nm, **BASE)
+    A = api.build_liouvillian(p)
+    Ar, perm = api.permute(A)
+    M = api.ilu_factor(Ar, d, fill, fp64_sweeps=True)
+    F = ilut(gpu_csr(Ar), d, fill)
+    ref = np.abs(F.solve(np.ones(Ar.N, dtype=complex))).max()
+    assert abs(api.ilu_condest(M, fp64=True) - ref) <= 1e-10 * ref
+    assert abs(api.ilu_condest(M) - ref) <= 1e-3 * ref
+
+
+def test_ilu_condest_flags_the_unstable_fill():
+    """The 40,000-row system with the 360,000-row parameters: ILUT(1e-5, 10)
+    leaves an unstable factor (estimate overflowing or astronomically large),
+    ILUT(1e-5, 100) a usable one -- the reason the solver workload uses p = 100."""
+    from paper_1411_4356_gb300 import MID
+    A = api.build_liouvillian(MID.params.with_(Nm=20), MID.trace_mode, MID.nth_floor)
+    Ar, perm = api.permute(A)
+    bad = api.ilu_condest(api.ilu_factor(Ar, MID.droptol, 10.0))
+    good = api.ilu_condest(api.ilu_factor(Ar, MID.droptol, MID.fill))
+    assert not np.isfinite(bad) or bad > 1e20
+    assert np.isfinite(good) and good < 1e12
+
+
 def test_complete_lu_solves_exactly():
     """d = 0 and no cap: M = A, so M^{-1} (A x) = x."""
     p = SystemParams(3, 5, **BASE)
