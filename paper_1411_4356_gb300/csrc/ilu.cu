@@ -21,7 +21,6 @@
 #include <cmath>
 #include <complex>
 #include <memory>
-#include <queue>
 #include <atomic>
 #include <cstdlib>
 #include <thread>
@@ -47,7 +46,9 @@ struct Picked {
 // Row-parallel ILUT on the host.  Rows are claimed in increasing order from
 // an atomic counter; a row eliminates with U rows of earlier rows as soon as
 // their owners publish them (release/acquire flags), so only eliminations
-// with recent rows wait.  Each row writes into preallocated slots sized by
+// with recent rows wait.  The working row is dense over the row's span and
+// is scanned in column order, which is the elimination order (fill from row
+// k only lands to the right of k).  Each row writes into preallocated slots sized by
 // the fill cap, compacted afterwards; the result is bitwise the same as the
 // serial elimination order.
 struct IlutShared {
@@ -72,11 +73,11 @@ void ilut_worker(IlutShared &S) {
     const auto &arp = *S.arp;
     const auto &aci = *S.aci;
     const auto &ava = *S.ava;
+    // dense working row; zero outside the current row's span [lo, hi]
     std::vector<cd> w(N, cd(0, 0));
-    std::vector<char> in_row(N, 0);
-    std::vector<int32_t> present;
+    double *wd = reinterpret_cast<double *>(w.data());
+    const double *ud = reinterpret_cast<const double *>(S.uva.data());
     std::vector<Picked> lo, hi;
-    std::priority_queue<int32_t, std::vector<int32_t>, std::greater<int32_t>> pending;
     auto by_size = [](const Picked &a, const Picked &b) { return a.mag != b.mag ? a.mag > b.mag : a.c < b.c; };
     auto by_col = [](const Picked &a, const Picked &b) { return a.c < b.c; };
     for (;;) {
@@ -88,23 +89,19 @@ void ilut_worker(IlutShared &S) {
         const double tau = S.droptol * anorm;
         int64_t cap = (int64_t)std::floor(S.fill * (double)nnz_i / 2.0);
         if (cap < 1) cap = 1;
-        present.clear();
-        for (int64_t e = arp[i]; e < arp[i + 1]; ++e) {
-            int32_t c = aci[e];
-            w[c] = cd(ava[e].x, ava[e].y);
-            in_row[c] = 1;
-            present.push_back(c);
-            if (c < i) pending.push(c);
+        // columns are sorted: the row spans [lo, hi]; fill only lands to the
+        // right of the column being eliminated, so the span grows at the top
+        int64_t span_lo = i, span_hi = i;
+        if (nnz_i > 0) {
+            span_lo = std::min<int64_t>(span_lo, aci[arp[i]]);
+            span_hi = std::max<int64_t>(span_hi, aci[arp[i + 1] - 1]);
         }
-        if (!in_row[i]) {
-            in_row[i] = 1;
-            w[i] = 0;
-            present.push_back((int32_t)i);
-        }
+        for (int64_t e = arp[i]; e < arp[i + 1]; ++e) w[aci[e]] = cd(ava[e].x, ava[e].y);
         double dropped = 0;
-        while (!pending.empty()) {
-            int32_t k = pending.top();
-            pending.pop();
+        // eliminate with the earlier rows in increasing column order; a zero
+        // entry (never filled, or cancelled exactly) has nothing to eliminate
+        for (int64_t k = span_lo; k < i; ++k) {
+            if (w[k] == cd(0, 0)) continue;
             for (int spins = 0; !S.done[k].load(std::memory_order_acquire); ++spins)
                 if (spins > 64) std::this_thread::yield();
             cd m = w[k] / S.diag[k];
@@ -115,20 +112,15 @@ void ilut_worker(IlutShared &S) {
             }
             w[k] = m;
             const int64_t ub = S.slot[k], ue = ub + S.ucnt[k];
+            if (ue == ub) continue;
+            span_hi = std::max<int64_t>(span_hi, S.uci[ue - 1]);
             // w -= m * (row k of U), in real arithmetic: the library complex
             // product guards against NaN operands on every call, which costs
             // several times the arithmetic in this innermost loop
             const double mr = m.real(), mi = m.imag();
-            double *wd = reinterpret_cast<double *>(w.data());
-            const double *ud = reinterpret_cast<const double *>(S.uva.data());
+            const int32_t *uc = S.uci.data();
             for (int64_t e = ub; e < ue; ++e) {
-                const int32_t c = S.uci[e];
-                if (!in_row[c]) {
-                    in_row[c] = 1;
-                    w[c] = 0;
-                    present.push_back(c);
-                    if (c < i) pending.push(c);
-                }
+                const int64_t c = uc[e];
                 const double ur = ud[2 * e], ui = ud[2 * e + 1];
                 wd[2 * c] -= mr * ur - mi * ui;
                 wd[2 * c + 1] -= mr * ui + mi * ur;
@@ -136,14 +128,14 @@ void ilut_worker(IlutShared &S) {
         }
         lo.clear();
         hi.clear();
-        for (int32_t c : present) {
-            if (c == i) continue;
-            double mg = std::abs(w[c]);
-            bool keep = w[c] != cd(0, 0) && !(mg < tau);
+        for (int64_t c = span_lo; c <= span_hi; ++c) {
+            if (c == i || w[c] == cd(0, 0)) continue;
+            const double mg = std::abs(w[c]);
+            const bool keep = !(mg < tau);
             if (c < i) {
-                if (keep) lo.push_back({c, mg});
+                if (keep) lo.push_back({(int32_t)c, mg});
             } else {
-                if (keep) hi.push_back({c, mg});
+                if (keep) hi.push_back({(int32_t)c, mg});
                 else dropped += mg;
             }
         }
@@ -180,10 +172,7 @@ void ilut_worker(IlutShared &S) {
         }
         S.ucnt[i] = (int32_t)hi.size();
         S.done[i].store(1, std::memory_order_release);
-        for (int32_t c : present) {
-            w[c] = 0;
-            in_row[c] = 0;
-        }
+        std::fill(w.begin() + span_lo, w.begin() + span_hi + 1, cd(0, 0));
     }
 }
 
