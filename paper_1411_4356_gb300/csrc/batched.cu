@@ -16,7 +16,9 @@
 // systems that reached their target.  At the end of a cycle each system
 // adds Z y to x, and its backward error eta (FP64, unmodified L) decides
 // whether it restarts.  Systems may have different sizes; each keeps its
-// own tiled factors and Krylov storage.
+// own tiled factors and Krylov storage.  When only a few systems are left,
+// those large enough for the split sweep over all SMs continue one by one
+// through om_steady_state_solve from their current iterate.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -35,6 +37,11 @@ constexpr int kBPS = 8;   // blocks per system for the vector kernels
 constexpr int kPrecondThreads = (tsw::kTileWarps + 1) * 32;
 constexpr int kWin = 8192, kStages = 8;
 constexpr int kMaxM = 64;
+constexpr int kTailSystems = 3;  // at most this many left: continue them one by one (split sweeps)
+
+bool split_capable(const om_ilu &F) {
+    return F.L.nunits > 0 && F.U.nunits > 0 && F.L.ntiles >= 4 * (int64_t)F.L.lag;
+}
 
 struct BSys {
     int64_t N;
@@ -352,9 +359,9 @@ __global__ void b_eta_finish(const BSys *sys, const int *active, int count, doub
 }
 
 // rho[perm[r]] = x[r] / trace(x), one block per system
-__global__ void b_normalise(const BSys *sys, int count, double *traces) {
+__global__ void b_normalise(const BSys *sys, const int *active, int count, double *traces) {
     const int s = blockIdx.x;
-    if (s >= count) return;
+    if (s >= count || !active[s]) return;
     const BSys &S = sys[s];
     __shared__ double2 red[kBT];
     double2 t = make_double2(0, 0);
@@ -481,11 +488,13 @@ void solve_lockstep(int32_t count, const om_matrix *const *A_rcm, const om_ilu *
 
         std::vector<int> done(count, 0), its(count, 0), cycles(count, 0), k(count, 0), act(count, 0);
         std::vector<double> xinf(count), eta(count, INFINITY), ests(2 * (size_t)count), target(count);
+        std::vector<double> tail_trace(count, 0.0);
         std::vector<om_status> st(count, OM_OK);
         for (int i = 0; i < count; ++i) xinf[i] = 1.0 / hs[i].n;
         auto upload_active = [&](const std::vector<int> &a) {
             OM_CUDA_TRY(cudaMemcpyAsync(dactive.p, a.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s));
         };
+        std::vector<int> handed(count, 0);
         for (;;) {
             int live = 0;
             for (int i = 0; i < count; ++i) {
@@ -495,6 +504,35 @@ void solve_lockstep(int32_t count, const om_matrix *const *A_rcm, const om_ilu *
                 k[i] = 0;
             }
             if (!live) break;
+            if (live <= kTailSystems) {
+                // the last few systems: the lock step would run one sweep
+                // block per system on an otherwise idle GPU, so systems whose
+                // sweeps split over all SMs continue one by one from their
+                // current iterate (same restarted GMRES, cycle by cycle)
+                bool any = false;
+                for (int i = 0; i < count; ++i) {
+                    if (!act[i] || !split_capable(*M[i])) continue;
+                    om_solve_opts o = *opts;
+                    o.max_iters = std::max(1, opts->max_iters - its[i]);
+                    om_solve_info one{};
+                    const om_status r = om_steady_state_solve(A_rcm[i], M[i], perm_dev[i], &o,
+                                                              reinterpret_cast<const double *>(hs[i].x), rho_dev[i],
+                                                              &one, reinterpret_cast<void *>(s));
+                    OM_REQUIRE(r == OM_OK || r == OM_ENOCONV || r == OM_ENUMERIC || r == OM_EBREAKDOWN,
+                               std::string("tail solve failed: ") + om_status_str(r));
+                    st[i] = r;
+                    for (int q = 0; q < one.cycles && cycles[i] + q < 64; ++q)
+                        if (info) info[i].residual_history[cycles[i] + q] = one.residual_history[q];
+                    its[i] += one.iterations;
+                    cycles[i] += one.cycles;
+                    eta[i] = one.eta;
+                    tail_trace[i] = one.trace_before;
+                    done[i] = 1;
+                    handed[i] = 1;
+                    any = true;
+                }
+                if (any) continue;
+            }
             // cycle start: r = b - A x, beta, v_0 = r / beta, g = beta e_1
             upload_active(act);
             b_spmv<<<gvec, kBT, 0, s>>>(dsys.p, dactive.p, -1);
@@ -590,7 +628,10 @@ void solve_lockstep(int32_t count, const om_matrix *const *A_rcm, const om_ilu *
             }
         }
         std::vector<double> tr(count);
-        b_normalise<<<(unsigned)count, kBT, 0, s>>>(dsys.p, count, dtrace.p);
+        std::vector<int> norm(count);
+        for (int i = 0; i < count; ++i) norm[i] = !handed[i];
+        upload_active(norm);
+        b_normalise<<<(unsigned)count, kBT, 0, s>>>(dsys.p, dactive.p, count, dtrace.p);
         omss::note_launch();
         OM_CHECK_LAUNCH();
         OM_CUDA_TRY(cudaMemcpyAsync(tr.data(), dtrace.p, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
@@ -602,7 +643,7 @@ void solve_lockstep(int32_t count, const om_matrix *const *A_rcm, const om_ilu *
                 info[i].iterations = its[i];
                 info[i].cycles = cycles[i];
                 info[i].eta = eta[i];
-                info[i].trace_before = tr[i];
+                info[i].trace_before = handed[i] ? tail_trace[i] : tr[i];
                 info[i].seconds = secs;
             }
         }
