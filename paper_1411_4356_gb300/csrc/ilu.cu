@@ -68,6 +68,32 @@ struct IlutShared {
     std::atomic<int64_t> guarded{0};
 };
 
+// w[c] -= m * u over the entries of one U row (columns strictly increasing,
+// so the four updates of a group never touch the same entry)
+inline void merge_row(double *__restrict__ wd, const int32_t *__restrict__ uc, const double *__restrict__ uv,
+                      int64_t n, double mr, double mi) {
+    int64_t e = 0;
+    for (; e + 4 <= n; e += 4) {
+        const int64_t c0 = uc[e], c1 = uc[e + 1], c2 = uc[e + 2], c3 = uc[e + 3];
+        const double r0 = uv[2 * e], i0 = uv[2 * e + 1], r1 = uv[2 * e + 2], i1 = uv[2 * e + 3];
+        const double r2 = uv[2 * e + 4], i2 = uv[2 * e + 5], r3 = uv[2 * e + 6], i3 = uv[2 * e + 7];
+        wd[2 * c0] -= mr * r0 - mi * i0;
+        wd[2 * c0 + 1] -= mr * i0 + mi * r0;
+        wd[2 * c1] -= mr * r1 - mi * i1;
+        wd[2 * c1 + 1] -= mr * i1 + mi * r1;
+        wd[2 * c2] -= mr * r2 - mi * i2;
+        wd[2 * c2 + 1] -= mr * i2 + mi * r2;
+        wd[2 * c3] -= mr * r3 - mi * i3;
+        wd[2 * c3 + 1] -= mr * i3 + mi * r3;
+    }
+    for (; e < n; ++e) {
+        const int64_t c = uc[e];
+        const double ur = uv[2 * e], ui = uv[2 * e + 1];
+        wd[2 * c] -= mr * ur - mi * ui;
+        wd[2 * c + 1] -= mr * ui + mi * ur;
+    }
+}
+
 void ilut_worker(IlutShared &S) {
     const int64_t N = S.N;
     const auto &arp = *S.arp;
@@ -118,13 +144,7 @@ void ilut_worker(IlutShared &S) {
             // product guards against NaN operands on every call, which costs
             // several times the arithmetic in this innermost loop
             const double mr = m.real(), mi = m.imag();
-            const int32_t *uc = S.uci.data();
-            for (int64_t e = ub; e < ue; ++e) {
-                const int64_t c = uc[e];
-                const double ur = ud[2 * e], ui = ud[2 * e + 1];
-                wd[2 * c] -= mr * ur - mi * ui;
-                wd[2 * c + 1] -= mr * ui + mi * ur;
-            }
+            merge_row(wd, S.uci.data() + ub, ud + 2 * ub, ue - ub, mr, mi);
         }
         lo.clear();
         hi.clear();
