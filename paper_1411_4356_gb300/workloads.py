@@ -44,6 +44,7 @@ class Workload:
     precision: int = 0
     trace_mode: str = "replace"
     nth_floor: float = 1e-15
+    refill: float = 100.0  # fill cap for a factor whose stability estimate fails
 
 
 # tiny: 1,600 rows, checked against dense LU
