@@ -203,6 +203,7 @@ extern "C" om_status om_steady_state_adjoint(const om_matrix *A, const om_ilu *M
                 if (cycles <= 64) inf.residual_history[cycles - 1] = r.last_estimate / gnorm;
                 if (r.breakdown) {
                     final_status = OM_EBREAKDOWN;
+                set_error("om_steady_state_adjoint: GMRES breakdown");
                     break;
                 }
                 if (r.iterations == 0 || rel <= opts->tol) break;
@@ -212,6 +213,7 @@ extern "C" om_status om_steady_state_adjoint(const om_matrix *A, const om_ilu *M
                 }
                 if (its >= opts->max_iters) {
                     final_status = OM_ENOCONV;
+                set_error("om_steady_state_adjoint: tolerance not reached within max_iters");
                     break;
                 }
             }

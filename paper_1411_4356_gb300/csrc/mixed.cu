@@ -118,6 +118,7 @@ om_status solve_mixed(const om_matrix *A, const om_ilu *M, const int32_t *perm_d
                 if (steps <= 64) inf.residual_history[steps - 1] = eta;
                 if (!std::isfinite(eta)) {
                     final_status = OM_ENUMERIC;
+                set_error("om_steady_state_solve (mixed precision): non-finite residual (unstable preconditioner?)");
                     break;
                 }
                 if (eta <= opts->tol) break;
@@ -125,6 +126,7 @@ om_status solve_mixed(const om_matrix *A, const om_ilu *M, const int32_t *perm_d
             if (!(beta > 0)) break;
             if (its >= opts->max_iters) {
                 final_status = OM_ENOCONV;
+                set_error("om_steady_state_solve (mixed precision): tolerance not reached within max_iters");
                 break;
             }
             // inner complex64 solve of A d = r / ||r||
@@ -147,6 +149,7 @@ om_status solve_mixed(const om_matrix *A, const om_ilu *M, const int32_t *perm_d
             ++steps;
             if (broke) {
                 final_status = OM_EBREAKDOWN;
+                set_error("om_steady_state_solve (mixed precision): GMRES breakdown");
                 break;
             }
         }

@@ -205,15 +205,18 @@ extern "C" om_status om_steady_state_solve(const om_matrix *A, const om_ilu *M, 
             if (cycles <= 64) inf.residual_history[cycles - 1] = eta;
             if (!std::isfinite(eta)) {
                 final_status = OM_ENUMERIC;
+                set_error("om_steady_state_solve: non-finite residual (unstable preconditioner?)");
                 break;
             }
             if (eta <= opts->tol) break;
             if (r.breakdown) {
                 final_status = OM_EBREAKDOWN;
+                set_error("om_steady_state_solve: GMRES breakdown");
                 break;
             }
             if (its >= opts->max_iters) {
                 final_status = OM_ENOCONV;
+                set_error("om_steady_state_solve: tolerance not reached within max_iters");
                 break;
             }
             if (r.iterations == 0) {  // residual already zero in FP64
