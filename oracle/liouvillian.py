@@ -109,8 +109,11 @@ def diagonal_positions(n: int) -> np.ndarray:
 
 def trace_weight(L: sp.csr_matrix) -> float:
     """w of Eq. 5: the mean of the diagonal of L (Sec. IV); its imaginary part
-    vanishes in exact arithmetic, so the real part is taken."""
-    return float(np.real(L.diagonal().sum()) / L.shape[0])
+    vanishes in exact arithmetic, so the real part is taken.  w only scales
+    the trace row; for a single level (n = 1) L = 0 and the mean is 0, so
+    w = 1 is taken there (any nonzero w gives rho = 1)."""
+    w = float(np.real(L.diagonal().sum()) / L.shape[0])
+    return w if w != 0.0 else 1.0
 
 
 def augmented(p: Params, trace_mode: str = "replace", nth_floor: float = 1e-15):

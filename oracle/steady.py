@@ -41,7 +41,10 @@ def eta(L: sp.csr_matrix, x: np.ndarray) -> float:
     """Normwise backward error ||L x||_inf / (||L||_inf ||x||_inf) with the
     unmodified Liouvillian L of Eq. 3 (no trace row)."""
     Linf = np.abs(L).sum(axis=1).max()
-    return float(np.abs(L @ x).max() / (Linf * np.abs(x).max()))
+    r = np.abs(L @ x).max()
+    if Linf == 0:  # L = 0 (a single level): every x has zero backward error
+        return 0.0 if r == 0 else float("inf")
+    return float(r / (Linf * np.abs(x).max()))
 
 
 @dataclass

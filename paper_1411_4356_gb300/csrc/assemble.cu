@@ -188,6 +188,9 @@ extern "C" om_status om_build_liouvillian(const om_params *params, const om_buil
         // Tr(a^dag a) = N_m N_c (N_c - 1)/2, Tr(b^dag b) = Tr(b b^dag) = N_c N_m (N_m - 1)/2;
         // the imaginary parts cancel exactly.
         A->w = -0.5 * (p.kappa * (p.Nc - 1) + Gm * (1.0 + 2.0 * nth) * (p.Nm - 1));
+        // w only scales the trace row: a single level (n = 1) has L = 0 and a
+        // zero mean, and any nonzero w then gives rho = 1
+        if (A->w == 0.0) A->w = 1.0;
 
         // row 0 of L and the trace row (host; n entries)
         int64_t c0[kMaxRow];

@@ -354,7 +354,7 @@ __global__ void b_eta_finish(const BSys *sys, const int *active, int count, doub
         a = fmax(a, S.scal[8 + q]);
         c = fmax(c, S.scal[8 + kBPS + q]);
     }
-    etas[s] = sqrt(a) / (S.norm_inf * sqrt(c));
+    etas[s] = S.norm_inf == 0 ? (a == 0 ? 0.0 : INFINITY) : sqrt(a) / (S.norm_inf * sqrt(c));
     xinf[s] = sqrt(c);
 }
 

@@ -123,6 +123,7 @@ double eta_of(const om_matrix &A, const double2 *x, double2 *y, GmresWork<double
     double ly = 0, lx = 0;
     dev_stats<double2>(y, A.N, W, s, nullptr, &ly);
     dev_stats<double2>(x, A.N, W, s, nullptr, &lx);
+    if (A.norm_inf == 0) return ly == 0 ? 0.0 : INFINITY;  // L = 0 (a single level)
     return ly / (A.norm_inf * lx);
 }
 

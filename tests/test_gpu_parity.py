@@ -230,3 +230,19 @@ def test_properties_at_larger_size():
     na = float(np.real(np.sum(c * np.diag(rho))))
     im_a = float(np.imag(np.trace(a @ rho)))
     assert p.kappa * na == pytest.approx(-2 * p.E * im_a, rel=1e-8, abs=1e-12)
+
+
+@pytest.mark.parametrize("mode", ["replace", "add"])
+def test_single_level_system(mode):
+    """The degenerate n = 1 system: L = 0, rho = 1 exactly."""
+    p = SystemParams(1, 1, **BASE)
+    A = api.build_liouvillian(p, mode)
+    Ar, perm = api.permute(A)
+    M = api.ilu_factor(Ar, 1e-4, 10.0)
+    rho, info = api.steady_state_solve(Ar, M, perm, tol=1e-12)
+    assert info.status == 0 and abs(complex(rho[0, 0].item()) - 1) < 1e-15
+
+
+def test_empty_batch():
+    rhos, infos = api.steady_state_solve_batched([])
+    assert rhos == [] and infos == []

@@ -156,3 +156,12 @@ def test_observables_definition():
     m = np.tile(np.arange(p.Nm), p.Nc)
     assert o["n_a"] == pytest.approx(float(np.real(np.sum(c * np.diag(rho)))), abs=1e-15)
     assert o["n_b"] == pytest.approx(float(np.real(np.sum(m * np.diag(rho)))), abs=1e-15)
+
+
+@pytest.mark.parametrize("mode", ["replace", "add"])
+def test_single_level_system_has_rho_one(mode):
+    """n = 1 (N_c = N_m = 1): L = 0, so the trace condition alone fixes rho = 1."""
+    from oracle.liouvillian import Params
+    p = Params(1, 1, 1.0, -1.0, 0.5, 0.3, 0.2, 1e3, 0.5)
+    r = steady_state_dense(p, mode)
+    assert r.rho.shape == (1, 1) and abs(r.rho[0, 0] - 1) < 1e-15
