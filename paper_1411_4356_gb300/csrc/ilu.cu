@@ -17,6 +17,7 @@
 // (tilesweep.cu): complex64 always, complex128 on request, and the
 // conjugate transposes U^H, L^H when the adjoint needs them.
 #include <algorithm>
+#include <functional>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -94,6 +95,45 @@ inline void merge_row(double *__restrict__ wd, const int32_t *__restrict__ uc, c
     }
 }
 
+// Relative margin between the squared modulus re^2 + im^2 (a few ulps of
+// rounding) and the exact modulus |w| (within one ulp), far above both.
+constexpr double kKeyEps = 1e-12;
+
+// Keeps in `v` (column order, .mag = squared modulus) the top K entries by
+// (exact modulus descending, column ascending) -- the largest moduli win,
+// ties go to the smaller column -- and leaves them in column order.  Keys
+// clear of the K-th key by the margin decide by themselves; the exact
+// modulus is computed only for the few entries within it.
+void select_top(std::vector<Picked> &v, int64_t K, const std::vector<cd> &w, std::vector<Picked> &band,
+                std::vector<int32_t> &chosen, std::vector<double> &keys) {
+    if ((int64_t)v.size() <= K) return;
+    if (K <= 0) {
+        v.clear();
+        return;
+    }
+    keys.clear();
+    for (const Picked &p : v) keys.push_back(p.mag);
+    std::nth_element(keys.begin(), keys.begin() + (K - 1), keys.end(), std::greater<double>());
+    const double kth = keys[K - 1];
+    const double hi_edge = kth * (1 + kKeyEps), lo_edge = kth * (1 - kKeyEps);
+    int64_t sure = 0;
+    band.clear();
+    for (const Picked &p : v) {
+        if (p.mag > hi_edge) ++sure;
+        else if (p.mag >= lo_edge) band.push_back({p.c, std::abs(w[p.c])});
+    }
+    std::sort(band.begin(), band.end(),
+              [](const Picked &a, const Picked &b) { return a.mag != b.mag ? a.mag > b.mag : a.c < b.c; });
+    chosen.clear();
+    for (int64_t t = 0; t < K - sure && t < (int64_t)band.size(); ++t) chosen.push_back(band[t].c);
+    std::sort(chosen.begin(), chosen.end());
+    size_t out = 0;
+    for (const Picked &p : v)
+        if (p.mag > hi_edge || (p.mag >= lo_edge && std::binary_search(chosen.begin(), chosen.end(), p.c)))
+            v[out++] = p;
+    v.resize(out);
+}
+
 void ilut_worker(IlutShared &S) {
     const int64_t N = S.N;
     const auto &arp = *S.arp;
@@ -103,7 +143,9 @@ void ilut_worker(IlutShared &S) {
     std::vector<cd> w(N, cd(0, 0));
     double *wd = reinterpret_cast<double *>(w.data());
     const double *ud = reinterpret_cast<const double *>(S.uva.data());
-    std::vector<Picked> lo, hi;
+    std::vector<Picked> lo, hi, band;
+    std::vector<int32_t> chosen;
+    std::vector<double> keys;
     auto by_size = [](const Picked &a, const Picked &b) { return a.mag != b.mag ? a.mag > b.mag : a.c < b.c; };
     auto by_col = [](const Picked &a, const Picked &b) { return a.c < b.c; };
     for (;;) {
@@ -148,29 +190,48 @@ void ilut_worker(IlutShared &S) {
         }
         lo.clear();
         hi.clear();
-        for (int64_t c = span_lo; c <= span_hi; ++c) {
-            if (c == i || w[c] == cd(0, 0)) continue;
-            const double mg = std::abs(w[c]);
-            const bool keep = !(mg < tau);
-            if (c < i) {
-                if (keep) lo.push_back({(int32_t)c, mg});
-            } else {
-                if (keep) hi.push_back({(int32_t)c, mg});
-                else dropped += mg;
+        if (S.compensate) {
+            // the dropped moduli are summed: every modulus is needed
+            for (int64_t c = span_lo; c <= span_hi; ++c) {
+                if (c == i || w[c] == cd(0, 0)) continue;
+                const double mg = std::abs(w[c]);
+                const bool keep = !(mg < tau);
+                if (c < i) {
+                    if (keep) lo.push_back({(int32_t)c, mg});
+                } else {
+                    if (keep) hi.push_back({(int32_t)c, mg});
+                    else dropped += mg;
+                }
             }
+            if ((int64_t)lo.size() > cap) {
+                std::nth_element(lo.begin(), lo.begin() + cap, lo.end(), by_size);
+                for (size_t t = cap; t < lo.size(); ++t) dropped += lo[t].mag * std::abs(S.diag[lo[t].c]);
+                lo.resize(cap);
+            }
+            if ((int64_t)hi.size() > cap - 1) {
+                std::nth_element(hi.begin(), hi.begin() + (cap - 1), hi.end(), by_size);
+                for (size_t t = cap - 1; t < hi.size(); ++t) dropped += hi[t].mag;
+                hi.resize(cap - 1);
+            }
+            std::sort(lo.begin(), lo.end(), by_col);
+            std::sort(hi.begin(), hi.end(), by_col);
+        } else {
+            // candidates in column order with the squared modulus as key; the
+            // exact modulus decides only where the key cannot (select_top)
+            const double t2 = tau * tau;
+            for (int64_t c = span_lo; c <= span_hi; ++c) {
+                if (c == i || w[c] == cd(0, 0)) continue;
+                const double re = w[c].real(), im = w[c].imag();
+                const double m2 = re * re + im * im;
+                bool keep;
+                if (m2 > t2 * (1 + kKeyEps)) keep = true;
+                else if (m2 < t2 * (1 - kKeyEps)) keep = false;
+                else keep = !(std::abs(w[c]) < tau);
+                if (keep) (c < i ? lo : hi).push_back({(int32_t)c, m2});
+            }
+            select_top(lo, cap, w, band, chosen, keys);
+            select_top(hi, cap - 1, w, band, chosen, keys);
         }
-        if ((int64_t)lo.size() > cap) {
-            std::nth_element(lo.begin(), lo.begin() + cap, lo.end(), by_size);
-            for (size_t t = cap; t < lo.size(); ++t) dropped += lo[t].mag * std::abs(S.diag[lo[t].c]);
-            lo.resize(cap);
-        }
-        if ((int64_t)hi.size() > cap - 1) {
-            std::nth_element(hi.begin(), hi.begin() + (cap - 1), hi.end(), by_size);
-            for (size_t t = cap - 1; t < hi.size(); ++t) dropped += hi[t].mag;
-            hi.resize(cap - 1);
-        }
-        std::sort(lo.begin(), lo.end(), by_col);
-        std::sort(hi.begin(), hi.end(), by_col);
         const int64_t base = S.slot[i];
         for (size_t t = 0; t < lo.size(); ++t) {
             S.lci[base + t] = lo[t].c;
