@@ -166,10 +166,34 @@ void ilut_worker(IlutShared &S) {
         }
         for (int64_t e = arp[i]; e < arp[i + 1]; ++e) w[aci[e]] = cd(ava[e].x, ava[e].y);
         double dropped = 0;
+        lo.clear();
+        hi.clear();
+        // drop test with the squared modulus as key; the exact modulus decides
+        // only where the key cannot
+        const double t2 = tau * tau;
+        auto candidate = [&](int64_t c, std::vector<Picked> &out) {
+            const double re = w[c].real(), im = w[c].imag();
+            const double m2 = re * re + im * im;
+            bool keep;
+            if (m2 > t2 * (1 + kKeyEps)) keep = true;
+            else if (m2 < t2 * (1 - kKeyEps)) keep = false;
+            else keep = !(std::abs(w[c]) < tau);
+            if (keep) out.push_back({(int32_t)c, m2});
+        };
+        // strict-L columns below the one being eliminated are final, so their
+        // candidates are collected while waiting for an earlier row
+        int64_t l_seen = span_lo;
+        auto collect_lo = [&](int64_t upto) {
+            for (int64_t c = l_seen; c < upto; ++c)
+                if (w[c] != cd(0, 0)) candidate(c, lo);
+            l_seen = upto;
+            if ((int64_t)lo.size() > 2 * cap) select_top(lo, cap, w, band, chosen, keys);
+        };
         // eliminate with the earlier rows in increasing column order; a zero
         // entry (never filled, or cancelled exactly) has nothing to eliminate
         for (int64_t k = span_lo; k < i; ++k) {
             if (w[k] == cd(0, 0)) continue;
+            if (!S.compensate && !S.done[k].load(std::memory_order_acquire)) collect_lo(k);
             for (int spins = 0; !S.done[k].load(std::memory_order_acquire); ++spins)
                 if (spins > 64) std::this_thread::yield();
             cd m = w[k] / S.diag[k];
@@ -188,8 +212,6 @@ void ilut_worker(IlutShared &S) {
             const double mr = m.real(), mi = m.imag();
             merge_row(wd, S.uci.data() + ub, ud + 2 * ub, ue - ub, mr, mi);
         }
-        lo.clear();
-        hi.clear();
         if (S.compensate) {
             // the dropped moduli are summed: every modulus is needed
             for (int64_t c = span_lo; c <= span_hi; ++c) {
@@ -216,19 +238,11 @@ void ilut_worker(IlutShared &S) {
             std::sort(lo.begin(), lo.end(), by_col);
             std::sort(hi.begin(), hi.end(), by_col);
         } else {
-            // candidates in column order with the squared modulus as key; the
-            // exact modulus decides only where the key cannot (select_top)
-            const double t2 = tau * tau;
-            for (int64_t c = span_lo; c <= span_hi; ++c) {
-                if (c == i || w[c] == cd(0, 0)) continue;
-                const double re = w[c].real(), im = w[c].imag();
-                const double m2 = re * re + im * im;
-                bool keep;
-                if (m2 > t2 * (1 + kKeyEps)) keep = true;
-                else if (m2 < t2 * (1 - kKeyEps)) keep = false;
-                else keep = !(std::abs(w[c]) < tau);
-                if (keep) (c < i ? lo : hi).push_back({(int32_t)c, m2});
-            }
+            // candidates in column order (the strict-L ones partly collected
+            // already); the top entries by exact modulus win (select_top)
+            collect_lo(i);
+            for (int64_t c = i + 1; c <= span_hi; ++c)
+                if (w[c] != cd(0, 0)) candidate(c, hi);
             select_top(lo, cap, w, band, chosen, keys);
             select_top(hi, cap - 1, w, band, chosen, keys);
         }
