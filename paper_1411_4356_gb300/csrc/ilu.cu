@@ -187,7 +187,7 @@ void ilut_worker(IlutShared &S) {
             for (int64_t c = l_seen; c < upto; ++c)
                 if (w[c] != cd(0, 0)) candidate(c, lo);
             l_seen = upto;
-            if ((int64_t)lo.size() > 2 * cap) select_top(lo, cap, w, band, chosen, keys);
+            if ((int64_t)lo.size() > cap) select_top(lo, cap, w, band, chosen, keys);
         };
         // eliminate with the earlier rows in increasing column order; a zero
         // entry (never filled, or cancelled exactly) has nothing to eliminate
