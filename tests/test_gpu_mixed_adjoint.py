@@ -127,4 +127,4 @@ def test_adjoint_at_40000_rows_against_central_differences():
 
     for t, name in ((1, "E"), (3, "kappa")):
         fd = (4 * central(name, 5e-5) - central(name, 1e-4)) / 3
-        assert g[t] == pytest.approx(fd, rel=1e-5), (name, g[t], fd)
+        assert g[t] == pytest.approx(fd, rel=1e-8), (name, g[t], fd)  # measured 1.5e-11
