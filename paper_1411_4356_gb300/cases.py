@@ -4,8 +4,10 @@
 
 builds the 40,000-row Liouvillian (N_c = 10, N_m = 20, the 360,000-row
 system's parameters), permutes it, factors it (d = 1e-5, p = 100) and runs
-the complex64 preconditioner solve three times; `spmv_10x20` runs the SpMV
+the complex64 preconditioner solve three times; `spmv_10x60` runs the SpMV
 three times instead.  Inputs are larger than L2 (the factors are ~0.4 GB).
+`batched_16` solves the first 16 draws of the 512-system sweep with the
+lock-step batched engine.
 """
 from __future__ import annotations
 
@@ -43,7 +45,23 @@ def spmv(Nc=10, Nm=60):
     print(f"spmv case: rows {Ar.N}, nnz {Ar.nnz}")
 
 
-CASES = {"sweep_10x20": lambda: sweep(10, 20), "spmv_10x60": lambda: spmv(10, 60)}
+def batched(count=16):
+    from .workloads import BATCH, batched_draws
+
+    systems = []
+    for p in batched_draws(count):
+        A = api.build_liouvillian(p, BATCH.trace_mode, BATCH.nth_floor)
+        Ar, perm = api.permute(A)
+        M = api.ilu_factor(Ar, BATCH.droptol, BATCH.fill)
+        if not (api.ilu_condest(M) < 1e12):
+            M = api.ilu_factor(Ar, BATCH.droptol, BATCH.refill)
+        systems.append((Ar, M, perm))
+    _, infos = api.steady_state_solve_batched(systems, restart=BATCH.restart, tol=BATCH.tol)
+    torch.cuda.synchronize()
+    print(f"batched case: {count} systems, iterations {[i.iterations for i in infos]}")
+
+
+CASES = {"sweep_10x20": lambda: sweep(10, 20), "spmv_10x60": lambda: spmv(10, 60), "batched_16": batched}
 
 if __name__ == "__main__":
     CASES[sys.argv[1]]()
