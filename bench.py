@@ -166,17 +166,17 @@ def run_omss(args):
 
     extra = {}
 
-    def step(readback: bool, precision: int = w.precision, condest: bool = False):
+    def step(readback: bool, precision: int = w.precision, condest: bool = False, fp64_sweeps: bool = False):
         h0 = time.perf_counter()
         A = api.build_liouvillian(p, w.trace_mode, w.nth_floor)
         Ar, perm = api.permute(A)
         A.free()
         h1 = time.perf_counter()
-        M = api.ilu_factor(Ar, w.droptol, w.fill)
+        M = api.ilu_factor(Ar, w.droptol, w.fill, fp64_sweeps=fp64_sweeps)
         if condest:  # outside the timed steps
             extra["condest"] = api.ilu_condest(M)
         _, info = api.steady_state_solve(Ar, M, perm, restart=w.restart, tol=w.tol, precision=precision,
-                                         rho_out=rho_dev)
+                                         rho_out=rho_dev, precond_fp64=fp64_sweeps)
         obs = api.observables(p.Nc, p.Nm, rho_dev)
         if readback:
             rho_host.copy_(rho_dev, non_blocking=True)
@@ -236,8 +236,16 @@ def run_omss(args):
     torch.cuda.synchronize()
     mixed_s = m0.elapsed_time(m1) / 1e3
     mixed_err = float((rho_dev - rho64).abs().max())
+    # ---- and with complex128 factors and sweeps: FP64 throughout (one step)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    fstat = step(False, fp64_sweeps=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    plain_s = f0.elapsed_time(f1) / 1e3
+    plain_err = float((rho_dev - rho64).abs().max())
 
-    elapsed, e2e_elapsed, mixed_s = max_over_ranks([device_s, e2e_elapsed, mixed_s], world, dist)
+    elapsed, e2e_elapsed, mixed_s, plain_s = max_over_ranks([device_s, e2e_elapsed, mixed_s, plain_s], world, dist)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -250,6 +258,11 @@ def run_omss(args):
              "iterations": mstat["iterations"], "eta": mstat["eta"],
              "max_abs_diff_vs_fp64_rho": mixed_err,
              "note": "same step with precision = 1: complex64 inner GMRES (SpMV, basis, sweeps) in FP64 refinement"}
+    fp64_plain = {"value": world / plain_s, "unit": "solves/s", "solve_s": fstat["solve_s"],
+                  "iterations": fstat["iterations"], "eta": fstat["eta"],
+                  "max_abs_diff_vs_value_rho": plain_err,
+                  "note": "same step FP64 throughout: complex128 factors and sweeps (one thread block per sweep; "
+                          "the split sweep is complex64 only); value uses FP64 GMRES with complex64 sweeps"}
 
     # algorithmic bytes: complex64 sweeps stream the strict factor (8-byte value
     # + 4-byte column), the row pointers and the vectors once per launch
@@ -304,6 +317,7 @@ def run_omss(args):
         "e2e": {"value": solves / e2e_elapsed, "unit": "solves/s", "h2d_bytes_per_step": 72,
                 "d2h_bytes_per_step": 16 * n * n},
         "mixed": mixed,
+        "fp64_plain": fp64_plain,
         "gpu_launches": int(launches),
         "clocks": clk,
         "krylov_gbs": krylov_bytes / solve_s / 1e9,
