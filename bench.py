@@ -328,7 +328,9 @@ def run_omss(args):
         "eta": s0["eta"],
         "ilu_condest": extra.get("condest"),
         "fill": s0["fill"],
-        "spmv": {"avg_launch_us": spmv_ms / max(spmv_n, 1) * 1e3, "launches": spmv_n},
+        "spmv": {"avg_launch_us": spmv_ms / max(spmv_n, 1) * 1e3, "launches": spmv_n,
+                 "achieved_gbs": spmv_b / (spmv_ms / max(spmv_n, 1) / 1e3) / 1e9 if spmv_ms > 0 else None,
+                 "note": "complex128 CSR, 4 lanes per row; FP64 arithmetic bounds it (4 DFMA per nonzero)"},
         "observables": {"n_a": s0["obs"][0], "n_b": s0["obs"][1]},
     }
     if world == 1 and not args.no_cpu_baseline:
