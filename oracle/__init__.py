@@ -14,7 +14,9 @@ legs of ``bench.py`` may import it.  It shares no code with the CUDA library
 Modules: ``liouvillian`` (Eq. 1-5, bandwidth/profile), ``reorder_factor``
 (RCM, ILUT, triangular sweeps; plain C in ``oracle_native.c``), ``gmres``
 (restarted right-preconditioned GMRES), ``steady`` (dense and iterative steady
-states, observables, adjoint gradients).
+states, observables, adjoint gradients), ``nojump`` (the no-jump part
+K rho + rho K^dag of Eq. 3 and its inverse, the second preconditioner of the
+GPU path).
 
 Every function is pinned by tests under ``tests/test_oracle_*.py`` to facts
 fixed by the paper or by the mathematics (the NNZ printed in Fig. 1, closed

@@ -90,3 +90,34 @@ def test_sweeps_against_dense_solves(seed):
     v = rng.standard_normal(n) + 1j * rng.standard_normal(n)
     np.testing.assert_allclose(F.solve(v), np.linalg.solve(M, v), rtol=1e-12, atol=1e-12)
     np.testing.assert_allclose(F.solve_h(v), np.linalg.solve(M.conj().T, v), rtol=1e-12, atol=1e-12)
+
+
+def test_hand_worked_fill_cap_with_ties():
+    """The fill cap binding in both parts, worked by hand (Sec. II: keep the
+    largest entries; ties go to the smaller column).
+
+    Rows 0-2 are diag(2).  d = 0, p = 0.7.
+    Row 3 = [4, 2, 2i, 5, 3, 3i]: nnz 6, cap floor(0.7*6/2) = 2.
+      L candidates 2, 1, i (moduli 2, 1, 1): col 0 and, of the tied cols 1
+      and 2, col 1.  U: cap - 1 = 1 entry besides the pivot 5; 3 and 3i tie,
+      col 4 is kept.
+    Row 4 = [1, -3, 0, 2, 6, -4]: nnz 5, cap floor(1.75) = 1.
+      Multipliers 0.5, -1.5 (rows 0, 1) and 2/5 = 0.4 (row 3, eliminated
+      although the cap drops it later): w4 = 6 - 0.4 * 3 = 4.8, w5 = -4.
+      L keeps the largest modulus, col 1 (-1.5, not the largest real part
+      0.5); U keeps no entry besides the pivot 4.8.
+    Row 5 = e5."""
+    A = np.zeros((6, 6), dtype=complex)
+    A[0, 0] = A[1, 1] = A[2, 2] = 2
+    A[3] = [4, 2, 2j, 5, 3, 3j]
+    A[4] = [1, -3, 0, 2, 6, -4]
+    A[5, 5] = 1
+    F = ilut(sp.csr_matrix(A), 0.0, 0.7)
+    Lx = np.zeros((6, 6), dtype=complex)
+    Lx[3, 0], Lx[3, 1] = 2, 1
+    Lx[4, 1] = -1.5
+    Ux = np.diag([2, 2, 2, 5, 4.8, 1]).astype(complex)
+    Ux[3, 4] = 3
+    np.testing.assert_allclose(F.L().toarray() - np.eye(6), Lx, atol=1e-15)
+    np.testing.assert_allclose(F.U().toarray(), Ux, atol=1e-15)
+    assert F.n_guarded == 0

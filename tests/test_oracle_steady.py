@@ -165,3 +165,32 @@ def test_single_level_system_has_rho_one(mode):
     p = Params(1, 1, 1.0, -1.0, 0.5, 0.3, 0.2, 1e3, 0.5)
     r = steady_state_dense(p, mode)
     assert r.rho.shape == (1, 1) and abs(r.rho[0, 0] - 1) < 1e-15
+
+
+def test_eta_hand_value():
+    """eta = ||L x||_inf / (||L||_inf ||x||_inf), worked by hand on a 3 x 3 L.
+
+    L = [[1, -2, 0], [0, 3, i], [2, 0, -1]], x = (1, i, -1):
+    L x = (1 - 2i, 2i, 3) -> ||L x||_inf = 3 (a 2-norm would give sqrt(18));
+    row sums of |L| are 3, 4, 3 -> ||L||_inf = 4; ||x||_inf = 1; eta = 0.75."""
+    import scipy.sparse as sp
+
+    from oracle.steady import eta
+
+    L = sp.csr_matrix(np.array([[1, -2, 0], [0, 3, 1j], [2, 0, -1]], dtype=complex))
+    x = np.array([1, 1j, -1], dtype=complex)
+    assert eta(L, x) == pytest.approx(0.75, rel=1e-15)
+    assert eta(L, 4 * x) == pytest.approx(0.75, rel=1e-15)  # scale invariant
+
+
+def test_dense_eta_uses_the_unmodified_liouvillian():
+    """The reported residual is that of L, not of L~: with the trace row the
+    converged x would leave L~ x - 0 = w e_0, an eta near |w| / ||L~||."""
+    from oracle.liouvillian import augmented
+
+    p = Params(3, 4, 1.0, -1.0, 0.5, 0.3, 0.2, 1e3, 0.5)
+    r = steady_state_dense(p)
+    Lt, b, w, L = augmented(p)
+    assert r.eta < 1e-14
+    lt_inf = np.abs(Lt).sum(axis=1).max()
+    assert np.abs(Lt @ r.x).max() / (lt_inf * np.abs(r.x).max()) > 1e-4
