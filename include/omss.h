@@ -202,6 +202,61 @@ om_status om_steady_state_solve_batched(int32_t count, const om_matrix *const *A
                                         om_solve_info *info, om_status *status, int32_t concurrency,
                                         void *stream);
 
+/* ---- the no-jump preconditioner ----------------------------------------------
+ * Eq. 3 splits as L rho = K rho + rho K^dag + sum_O gamma_O O rho O^dag with
+ * K = -i H - (kappa a^dag a + Gm (1 + n_th) b^dag b + Gm n_th b b^dag) / 2
+ * (H of Eq. 1, Gm = omega_m / Q_m, b b^dag taken in the truncated space).  In
+ * the basis of Eq. 4 the first two terms are S = I (x) K + conj(K) (x) I.  The
+ * paper does not use S; this library offers S^{-1} as a second preconditioner
+ * of the GMRES of Sec. IV beside the ILUT of Sec. II: applied exactly (four
+ * dense n x n products after the eigendecomposition K = V diag(lambda) V^{-1})
+ * it leaves GMRES a few tens of iterations on the systems of this library,
+ * and the steady state is the same (Eq. 5 fixes it).
+ *
+ * om_nojump_factor: builds K from params (n_th floored as in
+ * om_build_liouvillian when opts->nth_floor > 0), computes the
+ * eigendecomposition and V^{-1} on the device (cuSOLVER geev, getrf/getrs,
+ * complex128) and keeps the operands of the products.  flags bit 0: also keep
+ * the operands of S^{-H} (adjoint); bit 1: complex64 SIMT products instead of
+ * the TF32 tensor-core products.  Errors: OM_EINVAL (NULL, n*n > 2^31, non-
+ * finite parameters, or lambda_i + conj(lambda_j) = 0 for some i, j, i.e. an
+ * undamped mode), OM_ENUMERIC (the eigendecomposition or the inverse failed),
+ * OM_ENOMEM, OM_ECUDA.  The handle owns device memory (about 4 n^2 x 8 B, twice
+ * that with bit 0, plus the tensor-core operands of 16 n_pad^2 B each) and is
+ * released with om_nojump_free. */
+typedef struct om_nojump om_nojump;
+om_status om_nojump_factor(const om_params *params, const om_build_opts *opts, int32_t flags, void *stream,
+                           om_nojump **out);
+/* n (Hilbert dimension), whether the tensor-core products are in use,
+ * min |lambda_i + conj(lambda_j)| and the host wall time of the set-up phases
+ * (HOST double[3]: K and its eigendecomposition, V^{-1}, operand layout); any
+ * out pointer may be NULL. */
+om_status om_nojump_info(const om_nojump *M, int32_t *n, int32_t *tensor_cores, double *min_abs_d,
+                         double seconds[3]);
+/* z = S^{-1} v (flags bit 1: S^{-H} v, the handle must keep the adjoint
+ * operands), DEVICE c128 vectors of n*n entries in the column-stacked order of
+ * Eq. 4; z and v may alias.  The products run in complex64 or TF32 (flexible
+ * GMRES keeps the solve exact whatever the precision of the preconditioner).
+ * The handle's work matrices are used: calls on one handle must not overlap.
+ * Synchronises the stream.  Errors: OM_EINVAL, OM_ECUDA. */
+om_status om_nojump_apply(const om_nojump *M, int32_t flags, const double *v, double *z, void *stream);
+/* om_steady_state_solve with the no-jump preconditioner: A is the UNPERMUTED
+ * matrix of om_build_liouvillian (natural order, trace row 0), x0 (DEVICE c128
+ * [N], natural order) may be NULL, rho_dev as for om_steady_state_solve.
+ * precision 1 runs complex64 inner GMRES (complex64 SpMV and products) inside
+ * FP64 refinement.  Errors as om_steady_state_solve, plus OM_EINVAL for a
+ * permuted matrix or a handle of another size. */
+om_status om_steady_state_solve_nojump(const om_matrix *A, const om_nojump *M, const om_solve_opts *opts,
+                                       const double *x0, double *rho_dev, om_solve_info *info, void *stream);
+/* om_steady_state_adjoint with the no-jump preconditioner (S^{-H}) on the
+ * unpermuted matrix; the handle must keep the adjoint operands (flag 1) and
+ * opts->precision must be 0.  Arguments and errors as om_steady_state_adjoint. */
+om_status om_steady_state_adjoint_nojump(const om_matrix *A, const om_nojump *M, const om_solve_opts *opts,
+                                         const om_params *params, const double *rho_dev,
+                                         const double *grad_rho_dev, double grad_out[4], om_solve_info *info,
+                                         void *stream);
+void om_nojump_free(om_nojump *M);
+
 /* ---- single kernels, exposed for parity tests -------------------------------
  * y = A x (DEVICE c128 vectors of length nrows). */
 om_status om_spmv(const om_matrix *A, const double *x, double *y, void *stream);
@@ -244,8 +299,9 @@ om_status om_observables(int32_t Nc, int32_t Nm, const double *rho_dev, double o
 /* ---- instrumentation (no counterpart in the paper) -------------------------
  * om_kernel_launches: number of kernels the library has launched since it was
  * loaded.  om_profile(1) starts recording CUDA events around every one-block
- * triangular sweep (category 0), SpMV (category 1) and split sweep over all
- * SMs (category 2) launch, om_profile(0) stops, both
+ * triangular sweep (category 0), SpMV (category 1), split sweep over all
+ * SMs (category 2) and no-jump preconditioner application (category 3: its
+ * four products) launch, om_profile(0) stops, both
  * discard earlier records; om_profile_read returns the summed device time
  * (milliseconds, HOST out) and launch count of a category, synchronising on
  * the recorded events. */

@@ -20,8 +20,9 @@ its inverse out from that definition:
 * ``effective_hamiltonian`` -- K as a dense matrix, from the oracle's H and
   collapse operators (Eq. 1 and Eq. 3);
 * ``nojump_operator`` -- S as a sparse matrix (Kronecker products);
-* ``nojump_solve`` -- X with K X + X K^dag = Y (a Sylvester equation, solved
-  by SciPy's Bartels-Stewart routine), or with K^dag X + X K = Y for the
+* ``NoJumpInverse`` / ``nojump_solve`` -- X with K X + X K^dag = Y (a
+  Sylvester equation, solved by the Bartels-Stewart method: complex Schur form
+  of K, then a triangular Sylvester solve), or with K^dag X + X K = Y for the
   adjoint S^H;
 * ``nojump_solve_dense`` -- the same by dense LU of S (tiny sizes only);
 * ``steady_state_nojump`` -- GMRES on L~ (Eq. 5) right-preconditioned by
@@ -72,18 +73,34 @@ def jump_operator(p: Params, nth_floor: float = 1e-15) -> sp.csr_matrix:
     return J
 
 
+class NoJumpInverse:
+    """S^{-1} and S^{-H} by the Bartels-Stewart method: the complex Schur form
+    K = Q T Q^dag is computed once; then K X + X K^dag = Y becomes
+    T X' + X' T^dag = Q^dag Y Q (a triangular Sylvester equation, LAPACK
+    ztrsyl) with X = Q X' Q^dag."""
+
+    def __init__(self, p: Params, nth_floor: float = 1e-15, K: np.ndarray | None = None):
+        self.n = p.Nc * p.Nm
+        self.K = effective_hamiltonian(p, nth_floor) if K is None else K
+        self.T, self.Q = sla.schur(self.K, output="complex")
+
+    def __call__(self, y: np.ndarray, adjoint: bool = False) -> np.ndarray:
+        n, T, Q = self.n, self.T, self.Q
+        Y = np.asarray(y, dtype=np.complex128).reshape((n, n), order="F")
+        Yh = Q.conj().T @ Y @ Q
+        # forward: T X' + X' T^dag = Yh;  adjoint (K^dag X + X K = Y): T^dag X' + X' T = Yh
+        trana, tranb = ("C", "N") if adjoint else ("N", "C")
+        Xh, scale, info = sla.lapack.ztrsyl(T, T, Yh, trana=trana, tranb=tranb, isgn=1)
+        if info < 0:
+            raise ValueError(f"ztrsyl argument {-info}")
+        X = Q @ (Xh / scale) @ Q.conj().T
+        return X.reshape(-1, order="F")
+
+
 def nojump_solve(p: Params, y: np.ndarray, nth_floor: float = 1e-15, adjoint: bool = False,
                  K: np.ndarray | None = None) -> np.ndarray:
     """vec(X) with K X + X K^dag = Y (adjoint: K^dag X + X K = Y), Y = unvec(y)."""
-    n = p.Nc * p.Nm
-    if K is None:
-        K = effective_hamiltonian(p, nth_floor)
-    Y = np.asarray(y, dtype=np.complex128).reshape((n, n), order="F")
-    if adjoint:
-        X = sla.solve_sylvester(K.conj().T, K, Y)
-    else:
-        X = sla.solve_sylvester(K, K.conj().T, Y)
-    return X.reshape(-1, order="F")
+    return NoJumpInverse(p, nth_floor, K)(y, adjoint)
 
 
 def nojump_solve_dense(p: Params, y: np.ndarray, nth_floor: float = 1e-15, adjoint: bool = False) -> np.ndarray:
@@ -102,8 +119,7 @@ def steady_state_nojump(p: Params, trace_mode: str = "replace", nth_floor: float
 
     t0 = time.perf_counter()
     Lt, b, w, L = augmented(p, trace_mode, nth_floor)
-    K = effective_hamiltonian(p, nth_floor)
-    res = gmres_right(lambda v: Lt @ v, lambda v: nojump_solve(p, v, nth_floor, K=K), b, restart=restart,
-                      rtol=rtol, max_iterations=max_iterations)
+    Sinv = NoJumpInverse(p, nth_floor)
+    res = gmres_right(lambda v: Lt @ v, Sinv, b, restart=restart, rtol=rtol, max_iterations=max_iterations)
     x = trace_normalise(res.x, p.Nc * p.Nm)
     return x, res.iterations, res.converged, time.perf_counter() - t0

@@ -51,6 +51,17 @@ SIGNATURES = {
     "om_steady_state_solve_batched": (c_i32, [c_i32, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp), ctypes.POINTER(c_vp),
                                               ctypes.POINTER(om_solve_opts), ctypes.POINTER(c_vp),
                                               ctypes.POINTER(om_solve_info), ctypes.POINTER(c_i32), c_i32, c_vp]),
+    "om_nojump_factor": (c_i32, [ctypes.POINTER(om_params), ctypes.POINTER(om_build_opts), c_i32, c_vp,
+                                 ctypes.POINTER(c_vp)]),
+    "om_nojump_info": (c_i32, [c_vp, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32), ctypes.POINTER(c_dbl),
+                               ctypes.POINTER(c_dbl * 3)]),
+    "om_nojump_apply": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp]),
+    "om_steady_state_solve_nojump": (c_i32, [c_vp, c_vp, ctypes.POINTER(om_solve_opts), c_vp, c_vp,
+                                             ctypes.POINTER(om_solve_info), c_vp]),
+    "om_steady_state_adjoint_nojump": (c_i32, [c_vp, c_vp, ctypes.POINTER(om_solve_opts), ctypes.POINTER(om_params),
+                                               c_vp, c_vp, ctypes.POINTER(c_dbl * 4), ctypes.POINTER(om_solve_info),
+                                               c_vp]),
+    "om_nojump_free": (None, [c_vp]),
     "om_spmv": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
     "om_ilu_apply": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp]),
     "om_ilu_apply_noalloc": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp]),

@@ -199,6 +199,102 @@ def steady_state_adjoint(A_rcm: Matrix, M: ILU, perm: torch.Tensor, rho: torch.T
                                 list(info.residual_history[:min(info.cycles, 64)]), 0)
 
 
+class NoJump:
+    """Inverse of the no-jump part of Eq. 3 (om_nojump): the second preconditioner."""
+
+    def __init__(self, handle: int, params: SystemParams):
+        self._h = ctypes.c_void_p(handle)
+        self.params = params
+        n, tc, dmin = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        secs = (ctypes.c_double * 3)()
+        check(_lib.load().om_nojump_info(self._h, ctypes.byref(n), ctypes.byref(tc), ctypes.byref(dmin), secs),
+              "om_nojump_info")
+        self.n, self.tensor_cores, self.min_abs_d = n.value, bool(tc.value), dmin.value
+        # host seconds: K and its eigendecomposition, V^{-1}, operand layout
+        self.timings = dict(zip(("eig", "inverse", "layout"), list(secs)))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if self._h:
+            _lib.load().om_nojump_free(self._h)
+            self._h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def nojump_factor(params: SystemParams, nth_floor: float = 1e-15, adjoint: bool = False, simt: bool = False,
+                  eig32: bool = False, stream=None) -> NoJump:
+    """K = -i H - (1/2) sum gamma O^dag O and its eigendecomposition (om_nojump_factor);
+    adjoint=True keeps the operands of S^{-H}, simt=True selects complex64 SIMT products,
+    eig32=True computes the eigendecomposition in complex64."""
+    lib = _lib.load()
+    out = ctypes.c_void_p()
+    p = to_om_params(params)
+    o = om_build_opts(0, nth_floor)
+    flags = (1 if adjoint else 0) | (2 if simt else 0) | (4 if eig32 else 0)
+    check(lib.om_nojump_factor(ctypes.byref(p), ctypes.byref(o), flags, ctypes.c_void_p(_stream(stream)),
+                               ctypes.byref(out)), "om_nojump_factor")
+    return NoJump(out.value, params)
+
+
+def nojump_apply(M: NoJump, v: torch.Tensor, adjoint: bool = False, stream=None) -> torch.Tensor:
+    """z = S^{-1} v (adjoint: S^{-H} v) for a CUDA complex128 vector of n*n entries."""
+    _require_cuda(v, torch.complex128, M.n * M.n, "v")
+    z = torch.empty_like(v)
+    check(_lib.load().om_nojump_apply(M.handle, 2 if adjoint else 0, _ptr(v), _ptr(z),
+                                      ctypes.c_void_p(_stream(stream))), "om_nojump_apply")
+    return z
+
+
+def steady_state_solve_nojump(A: Matrix, M: NoJump, restart: int = 50, max_iters: int = 5000, tol: float = 1e-10,
+                              precision: int = 0, x0: torch.Tensor | None = None, stream=None,
+                              raise_on_noconv: bool = True, rho_out: torch.Tensor | None = None):
+    """Sec. IV's GMRES on the unpermuted L~ with the no-jump preconditioner:
+    rho (n x n complex128 CUDA tensor) and SolveInfo."""
+    lib = _lib.load()
+    n = A.params.Nc * A.params.Nm
+    flat = rho_out if rho_out is not None else torch.empty(n * n, dtype=torch.complex128, device="cuda")
+    _require_cuda(flat, torch.complex128, n * n, "rho_out")
+    if x0 is not None:
+        _require_cuda(x0, torch.complex128, A.N, "x0")
+    o = _opts(restart, max_iters, tol, precision, 0)
+    info = om_solve_info()
+    st = lib.om_steady_state_solve_nojump(A.handle, M.handle, ctypes.byref(o), _ptr(x0), _ptr(flat),
+                                          ctypes.byref(info), ctypes.c_void_p(_stream(stream)))
+    si = SolveInfo(info.iterations, info.cycles, info.eta, info.trace_before, info.seconds,
+                   list(info.residual_history[:min(info.cycles, 64)]), st)
+    if st != 0 and not (st == -5 and not raise_on_noconv):
+        check(st, "om_steady_state_solve_nojump")
+    return flat.view(n, n).t(), si
+
+
+def steady_state_adjoint_nojump(A: Matrix, M: NoJump, rho: torch.Tensor, grad_rho: torch.Tensor, restart: int = 50,
+                                max_iters: int = 5000, tol: float = 1e-12, stream=None):
+    """dF/d(Delta, E, g0, kappa) with the no-jump preconditioner (S^{-H})."""
+    lib = _lib.load()
+    n = A.params.Nc * A.params.Nm
+    rho_flat = rho.t().contiguous().view(-1) if rho.dim() == 2 else rho
+    g_flat = grad_rho.t().contiguous().view(-1) if grad_rho.dim() == 2 else grad_rho.contiguous()
+    _require_cuda(rho_flat, torch.complex128, n * n, "rho")
+    _require_cuda(g_flat, torch.complex128, n * n, "grad_rho")
+    o = _opts(restart, max_iters, tol, 0, 0)
+    p = to_om_params(A.params)
+    out = (ctypes.c_double * 4)()
+    info = om_solve_info()
+    check(lib.om_steady_state_adjoint_nojump(A.handle, M.handle, ctypes.byref(o), ctypes.byref(p), _ptr(rho_flat),
+                                             _ptr(g_flat), ctypes.byref(out), ctypes.byref(info),
+                                             ctypes.c_void_p(_stream(stream))), "om_steady_state_adjoint_nojump")
+    return list(out), SolveInfo(info.iterations, info.cycles, info.eta, info.trace_before, info.seconds,
+                                list(info.residual_history[:min(info.cycles, 64)]), 0)
+
+
 def spmv(A: Matrix, x: torch.Tensor, stream=None) -> torch.Tensor:
     _require_cuda(x, torch.complex128, A.N, "x")
     y = torch.empty_like(x)
@@ -240,7 +336,7 @@ def kernel_launches() -> int:
     return int(_lib.load().om_kernel_launches())
 
 
-PROF_SWEEP, PROF_SPMV, PROF_SPLIT = 0, 1, 2
+PROF_SWEEP, PROF_SPMV, PROF_SPLIT, PROF_NOJUMP = 0, 1, 2, 3
 
 
 def profile(enable: bool) -> None:

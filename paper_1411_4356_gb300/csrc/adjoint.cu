@@ -23,13 +23,13 @@ namespace {
 __global__ void gather_perm(const double2 *__restrict__ src, const int32_t *__restrict__ perm, int64_t N,
                             double2 *__restrict__ dst) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N; r += stride) dst[r] = src[perm[r]];
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N; r += stride) dst[r] = src[perm ? perm[r] : r];
 }
 
 __global__ void scatter_perm(const double2 *__restrict__ src, const int32_t *__restrict__ perm, int64_t N,
                              double2 *__restrict__ dst) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N; r += stride) dst[perm[r]] = src[r];
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N; r += stride) dst[perm ? perm[r] : r] = src[r];
 }
 
 constexpr int kThreads = 256;
@@ -119,6 +119,16 @@ struct AdjointOps : KrylovOps<double2> {
     }
 };
 
+// natural order: L~^H with the preconditioner S^{-H} of the no-jump part
+struct NojumpAdjointOps : KrylovOps<double2> {
+    const om_matrix *A;
+    const om_nojump *M;
+    void apply(const double2 *v, double2 *out, cudaStream_t s) override {
+        spmv_c128(A->h_rowptr.p, A->h_col.p, A->h_val.p, A->N, v, out, s);
+    }
+    void precond(const double2 *v, double2 *out, cudaStream_t s) override { nojump_apply_c128(*M, true, v, out, s); }
+};
+
 // A^H in CSR (host transpose by counting, so the entry order is deterministic)
 void ensure_conj_transpose(const om_matrix &A, cudaStream_t s) {
     if (A.h_rowptr.p) return;
@@ -155,16 +165,17 @@ void ensure_conj_transpose(const om_matrix &A, cudaStream_t s) {
 
 using namespace omss;
 
-extern "C" om_status om_steady_state_adjoint(const om_matrix *A, const om_ilu *M, const int32_t *perm_dev,
-                                             const om_solve_opts *opts, const om_params *params,
-                                             const double *rho_dev, const double *grad_rho_dev, double grad_out[4],
-                                             om_solve_info *info, void *stream) {
+namespace omss {
+namespace {
+// GMRES on A^H mu = G (G permuted into the solver's order by perm, NULL =
+// natural order) and the contraction dF/dtheta = -Re(mu^H dA/dtheta rho).
+// `make_ops` builds the operator/preconditioner pair around the work space.
+template <class MakeOps>
+om_status adjoint_solve(const om_matrix *A, const int32_t *perm_dev, const om_solve_opts *opts,
+                        const double *rho_dev, const double *grad_rho_dev, double grad_out[4], om_solve_info *info,
+                        void *stream, MakeOps make_ops) {
     om_status final_status = OM_OK;
     om_status st = guarded([&] {
-        check_solve_args(A, M, perm_dev, opts);
-        OM_REQUIRE(params && rho_dev && grad_rho_dev && grad_out, "om_steady_state_adjoint: NULL argument");
-        OM_REQUIRE(M->has_transpose, "the factor was built without conjugate transposes (om_ilu_factor flag 2)");
-        OM_REQUIRE(params->Nc == A->params.Nc && params->Nm == A->params.Nm, "params do not match the matrix");
         auto t0 = std::chrono::steady_clock::now();
         cudaStream_t s = as_stream(stream);
         const int64_t N = A->N;
@@ -185,11 +196,7 @@ extern "C" om_status om_steady_state_adjoint(const om_matrix *A, const om_ilu *M
         dev_zero(mu.p, N, s);
         double gnorm = 0;
         dev_stats<double2>(g.p, N, W, s, &gnorm, nullptr);
-        AdjointOps ops;
-        ops.A = A;
-        ops.M = M;
-        ops.fp64_precond = opts->precond_fp64 != 0;
-        ops.tmp32 = W.tmp32.p;
+        auto ops = make_ops(W);
         om_solve_info inf{};
         int its = 0, cycles = 0;
         double rel = INFINITY;
@@ -245,4 +252,53 @@ extern "C" om_status om_steady_state_adjoint(const om_matrix *A, const om_ilu *M
         sums.release(s);
     });
     return st != OM_OK ? st : final_status;
+}
+}  // namespace
+}  // namespace omss
+
+extern "C" om_status om_steady_state_adjoint(const om_matrix *A, const om_ilu *M, const int32_t *perm_dev,
+                                             const om_solve_opts *opts, const om_params *params,
+                                             const double *rho_dev, const double *grad_rho_dev, double grad_out[4],
+                                             om_solve_info *info, void *stream) {
+    om_status st = guarded([&] {
+        check_solve_args(A, M, perm_dev, opts);
+        OM_REQUIRE(params && rho_dev && grad_rho_dev && grad_out, "om_steady_state_adjoint: NULL argument");
+        OM_REQUIRE(M->has_transpose, "the factor was built without conjugate transposes (om_ilu_factor flag 2)");
+        OM_REQUIRE(params->Nc == A->params.Nc && params->Nm == A->params.Nm, "params do not match the matrix");
+    });
+    if (st != OM_OK) return st;
+    return adjoint_solve(A, perm_dev, opts, rho_dev, grad_rho_dev, grad_out, info, stream,
+                         [&](GmresWork<double2> &W) {
+                             AdjointOps ops;
+                             ops.A = A;
+                             ops.M = M;
+                             ops.fp64_precond = opts->precond_fp64 != 0;
+                             ops.tmp32 = W.tmp32.p;
+                             return ops;
+                         });
+}
+
+namespace omss {
+void check_nojump_args(const om_matrix *A, const om_nojump *M, const om_solve_opts *o);
+}
+
+extern "C" om_status om_steady_state_adjoint_nojump(const om_matrix *A, const om_nojump *M,
+                                                    const om_solve_opts *opts, const om_params *params,
+                                                    const double *rho_dev, const double *grad_rho_dev,
+                                                    double grad_out[4], om_solve_info *info, void *stream) {
+    om_status st = guarded([&] {
+        check_nojump_args(A, M, opts);
+        OM_REQUIRE(opts->precision == 0, "om_steady_state_adjoint_nojump: precision must be 0");
+        OM_REQUIRE(params && rho_dev && grad_rho_dev && grad_out, "om_steady_state_adjoint_nojump: NULL argument");
+        OM_REQUIRE(M->has_adjoint, "the no-jump handle was built without the adjoint operands (flag 1)");
+        OM_REQUIRE(params->Nc == A->params.Nc && params->Nm == A->params.Nm, "params do not match the matrix");
+    });
+    if (st != OM_OK) return st;
+    return adjoint_solve(A, nullptr, opts, rho_dev, grad_rho_dev, grad_out, info, stream,
+                         [&](GmresWork<double2> &) {
+                             NojumpAdjointOps ops;
+                             ops.A = A;
+                             ops.M = M;
+                             return ops;
+                         });
 }

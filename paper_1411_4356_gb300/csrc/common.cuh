@@ -19,8 +19,9 @@ void set_error(const std::string &msg);
 void note_launch();
 
 // Kernel timing by CUDA events, active between om_profile(1) and om_profile(0).
-// Categories: 0 = one-block triangular sweeps, 1 = SpMV, 2 = split sweeps.
-enum { PROF_SWEEP = 0, PROF_SPMV = 1, PROF_SPLIT = 2, PROF_CATEGORIES = 3 };
+// Categories: 0 = one-block triangular sweeps, 1 = SpMV, 2 = split sweeps,
+// 3 = no-jump preconditioner applications (four products each).
+enum { PROF_SWEEP = 0, PROF_SPMV = 1, PROF_SPLIT = 2, PROF_NOJUMP = 3, PROF_CATEGORIES = 4 };
 struct ProfScope {
     int cat;
     cudaStream_t s;
@@ -205,6 +206,47 @@ struct om_ilu {
     cudaStream_t owner_stream = nullptr;
     ~om_ilu();
 };
+
+// Inverse of the no-jump part of Eq. 3 (nojump.cu).  L rho = K rho + rho K^dag
+// + sum_O gamma_O O rho O^dag with K = -i H - (1/2) sum_O gamma_O O^dag O; the
+// first two terms form S = I (x) K + conj(K) (x) I in the basis of Eq. 4.
+// With K = V diag(lambda) V^{-1},
+//   S^{-1}(Y) = V [(V^{-1} Y V^{-H}) ./ D] V^H,   D_ij = lambda_i + conj(lambda_j),
+//   S^{-H}(X) = V^{-H} [(V^H X V) ./ conj(D)] V^{-1},
+// each four dense n x n complex products.
+namespace omss {
+struct NojumpTc;  // tensor maps and status word of the tensor-core products (nojump_tc.cu)
+}
+struct om_nojump {
+    int32_t n = 0, Nc = 0, Nm = 0;
+    bool has_adjoint = false;
+    bool tensor_cores = false;   // TF32 tcgen05 products (else complex64 SIMT products)
+    double seconds[3] = {0, 0, 0};  // host wall time: K and its eigendecomposition, V^{-1}, operand layout
+    double min_abs_d = 0;        // min |lambda_i + conj(lambda_j)| (the smallest divisor)
+    omss::DBuf<float2> lam32;    // eigenvalues of K, complex64 (n)
+    // row-major complex64 operands A of the products C = A B:
+    // forward Vi, conj(Vi), V, conj(V); adjoint V^H, V^T, Vi^H, Vi^T
+    omss::DBuf<float2> op[8];
+    // the same operands expanded for the tensor cores (tcgen05.cu): each
+    // complex entry a becomes the real 2 x 2 block [[re, -im], [im, re]],
+    // row-major fp32, rows and columns padded to a multiple of 128
+    omss::DBuf<float> opx[8];
+    int32_t n_pad = 0;           // padded complex dimension of opx
+    omss::NojumpTc *tc = nullptr;
+    omss::DBuf<float2> t0, t1, t2;  // n*n complex64 work matrices of one apply
+    cudaStream_t owner_stream = nullptr;
+    ~om_nojump();
+};
+
+namespace omss {
+
+// z = S^{-1} v (or S^{-H} v) with complex64 or complex128 vectors of length
+// n*n in the column-stacked order of Eq. 4 (v and z may alias).  Uses the
+// handle's work matrices: one apply per handle at a time.
+void nojump_apply_c64(const om_nojump &M, bool adjoint, const float2 *v, float2 *z, cudaStream_t s);
+void nojump_apply_c128(const om_nojump &M, bool adjoint, const double2 *v, double2 *z, cudaStream_t s);
+
+}  // namespace omss
 
 namespace omss {
 

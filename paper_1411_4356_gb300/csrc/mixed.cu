@@ -64,6 +64,16 @@ struct InnerOps : KrylovOps<float2> {
     }
 };
 
+// complex64 inner solve with the no-jump preconditioner (natural order)
+struct NojumpInnerOps : KrylovOps<float2> {
+    const om_matrix *A;
+    const om_nojump *M;
+    void apply(const float2 *v, float2 *out, cudaStream_t s) override {
+        spmv_c64(A->rowptr.p, A->col.p, A->val32.p, A->N, v, out, s);
+    }
+    void precond(const float2 *v, float2 *out, cudaStream_t s) override { nojump_apply_c64(*M, false, v, out, s); }
+};
+
 }  // namespace
 
 void ensure_values_c64(const om_matrix &A, cudaStream_t s) {
@@ -74,12 +84,12 @@ void ensure_values_c64(const om_matrix &A, cudaStream_t s) {
     OM_CHECK_LAUNCH();
 }
 
-om_status solve_mixed(const om_matrix *A, const om_ilu *M, const int32_t *perm_dev, const om_solve_opts *opts,
+namespace {
+// the refinement loop around an inner complex64 operator/preconditioner pair
+om_status mixed_solve(const om_matrix *A, KrylovOps<float2> &ops, const int32_t *perm_dev, const om_solve_opts *opts,
                       const double *x0, double *rho_dev, om_solve_info *info, void *stream) {
     om_status final_status = OM_OK;
     om_status st = guarded([&] {
-        check_solve_args(A, M, perm_dev, opts);
-        OM_REQUIRE(rho_dev, "rho_dev is NULL");
         auto t0 = std::chrono::steady_clock::now();
         cudaStream_t s = as_stream(stream);
         const int64_t N = A->N;
@@ -100,9 +110,6 @@ om_status solve_mixed(const om_matrix *A, const om_ilu *M, const int32_t *perm_d
         OM_CHECK_LAUNCH();
         if (x0) dev_copy(reinterpret_cast<const double2 *>(x0), x.p, N, s);
         else dev_zero(x.p, N, s);
-        InnerOps ops;
-        ops.A = A;
-        ops.M = M;
         om_solve_info inf{};
         double eta = INFINITY;
         int its = 0, steps = 0;
@@ -170,6 +177,35 @@ om_status solve_mixed(const om_matrix *A, const om_ilu *M, const int32_t *perm_d
         d32.release(s);
     });
     return st != OM_OK ? st : final_status;
+}
+}  // namespace
+
+om_status solve_mixed(const om_matrix *A, const om_ilu *M, const int32_t *perm_dev, const om_solve_opts *opts,
+                      const double *x0, double *rho_dev, om_solve_info *info, void *stream) {
+    om_status st = guarded([&] {
+        check_solve_args(A, M, perm_dev, opts);
+        OM_REQUIRE(rho_dev, "rho_dev is NULL");
+    });
+    if (st != OM_OK) return st;
+    InnerOps ops;
+    ops.A = A;
+    ops.M = M;
+    return mixed_solve(A, ops, perm_dev, opts, x0, rho_dev, info, stream);
+}
+
+void check_nojump_args(const om_matrix *A, const om_nojump *M, const om_solve_opts *o);
+
+om_status solve_mixed_nojump(const om_matrix *A, const om_nojump *M, const om_solve_opts *opts, const double *x0,
+                             double *rho_dev, om_solve_info *info, void *stream) {
+    om_status st = guarded([&] {
+        check_nojump_args(A, M, opts);
+        OM_REQUIRE(rho_dev, "rho_dev is NULL");
+    });
+    if (st != OM_OK) return st;
+    NojumpInnerOps ops;
+    ops.A = A;
+    ops.M = M;
+    return mixed_solve(A, ops, nullptr, opts, x0, rho_dev, info, stream);
 }
 
 }  // namespace omss

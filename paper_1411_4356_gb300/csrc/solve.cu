@@ -43,7 +43,7 @@ __global__ void gather_sum(const double2 *x, const int32_t *pos, int n, double2 
     }
 }
 
-// rho[perm[r]] = x[r] / t
+// rho[perm[r]] = x[r] / t (perm NULL: natural order)
 __global__ void normalise_scatter(const double2 *__restrict__ x, const int32_t *__restrict__ perm, int64_t N,
                                   const double2 *t, double2 *__restrict__ rho) {
     const double2 tt = t[0];
@@ -51,7 +51,7 @@ __global__ void normalise_scatter(const double2 *__restrict__ x, const int32_t *
     const double2 inv = make_double2(tt.x / d, -tt.y / d);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N; r += stride)
-        rho[perm[r]] = cmul(x[r], inv);
+        rho[perm ? perm[r] : r] = cmul(x[r], inv);
 }
 
 // <a^dag a> = sum_h c(h) rho_hh, <b^dag b> = sum_h m(h) rho_hh
@@ -88,6 +88,18 @@ struct ForwardOps : KrylovOps<double2> {
     }
     void precond(const double2 *v, double2 *out, cudaStream_t s) override {
         precond_apply(*M, false, fp64_precond, v, out, tmp32, s);
+    }
+};
+
+// GMRES on the unpermuted L~ with the no-jump preconditioner S^{-1}
+struct NojumpOps : KrylovOps<double2> {
+    const om_matrix *A;
+    const om_nojump *M;
+    void apply(const double2 *v, double2 *out, cudaStream_t s) override {
+        spmv_c128(A->rowptr.p, A->col.p, A->val.p, A->N, v, out, s);
+    }
+    void precond(const double2 *v, double2 *out, cudaStream_t s) override {
+        nojump_apply_c128(*M, false, v, out, s);
     }
 };
 
@@ -166,19 +178,16 @@ om_status solve_mixed(const om_matrix *A, const om_ilu *M, const int32_t *perm_d
                       const double *x0, double *rho_dev, om_solve_info *info, void *stream);
 }
 
-extern "C" om_status om_steady_state_solve(const om_matrix *A, const om_ilu *M, const int32_t *perm_dev,
-                                           const om_solve_opts *opts, const double *x0, double *rho_dev,
-                                           om_solve_info *info, void *stream) {
-    if (opts && opts->precision == 1) return solve_mixed(A, M, perm_dev, opts, x0, rho_dev, info, stream);
+namespace omss {
+// The FP64 restarted GMRES of Sec. IV around a given operator/preconditioner
+// pair; perm (NULL: natural order) scatters the normalised x into rho.
+om_status fp64_solve(const om_matrix *A, KrylovOps<double2> &ops, GmresWork<double2> &W, const int32_t *perm_dev,
+                     const om_solve_opts *opts, const double *x0, double *rho_dev, om_solve_info *info,
+                     cudaStream_t s) {
     om_status final_status = OM_OK;
     om_status st = guarded([&] {
-        check_solve_args(A, M, perm_dev, opts);
-        OM_REQUIRE(rho_dev, "rho_dev is NULL");
         auto t0 = std::chrono::steady_clock::now();
-        cudaStream_t s = as_stream(stream);
         const int64_t N = A->N;
-        GmresWork<double2> W;
-        W.alloc(N, opts->restart, s);
         DBuf<double2> b, x;
         b.alloc(N, s);
         x.alloc(N, s);
@@ -187,11 +196,6 @@ extern "C" om_status om_steady_state_solve(const om_matrix *A, const om_ilu *M, 
         OM_CHECK_LAUNCH();
         if (x0) dev_copy(reinterpret_cast<const double2 *>(x0), x.p, N, s);
         else dev_zero(x.p, N, s);
-        ForwardOps ops;
-        ops.A = A;
-        ops.M = M;
-        ops.fp64_precond = opts->precond_fp64 != 0;
-        ops.tmp32 = W.tmp32.p;
         om_solve_info inf{};
         double xinf = 1.0 / A->n;
         double eta = INFINITY;
@@ -233,11 +237,72 @@ extern "C" om_status om_steady_state_solve(const om_matrix *A, const om_ilu *M, 
         inf.trace_before = tr.x;
         inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (info) *info = inf;
-        W.release(s);
         b.release(s);
         x.release(s);
     });
     return st != OM_OK ? st : final_status;
+}
+
+void check_nojump_args(const om_matrix *A, const om_nojump *M, const om_solve_opts *o) {
+    OM_REQUIRE(A && M && o, "NULL argument");
+    OM_REQUIRE(!A->permuted, "the no-jump preconditioner works in the natural order of Eq. 4: pass the matrix of "
+                             "om_build_liouvillian, not of om_permute");
+    OM_REQUIRE(M->Nc == A->params.Nc && M->Nm == A->params.Nm, "the no-jump handle and the matrix differ in size");
+    OM_REQUIRE(o->restart >= 1 && o->restart <= 120, "restart must be in [1, 120]");
+    OM_REQUIRE(o->max_iters >= 1, "max_iters must be >= 1");
+    OM_REQUIRE(o->tol > 0, "tol must be positive");
+    OM_REQUIRE(o->precision == 0 || o->precision == 1, "precision must be 0 or 1");
+}
+om_status solve_mixed_nojump(const om_matrix *A, const om_nojump *M, const om_solve_opts *opts, const double *x0,
+                             double *rho_dev, om_solve_info *info, void *stream);
+}  // namespace omss
+
+extern "C" om_status om_steady_state_solve(const om_matrix *A, const om_ilu *M, const int32_t *perm_dev,
+                                           const om_solve_opts *opts, const double *x0, double *rho_dev,
+                                           om_solve_info *info, void *stream) {
+    if (opts && opts->precision == 1) return solve_mixed(A, M, perm_dev, opts, x0, rho_dev, info, stream);
+    cudaStream_t s = as_stream(stream);
+    GmresWork<double2> W;
+    om_status st = guarded([&] {
+        check_solve_args(A, M, perm_dev, opts);
+        OM_REQUIRE(rho_dev, "rho_dev is NULL");
+        W.alloc(A->N, opts->restart, s);
+    });
+    if (st != OM_OK) {
+        W.release(s);
+        return st;
+    }
+    ForwardOps ops;
+    ops.A = A;
+    ops.M = M;
+    ops.fp64_precond = opts->precond_fp64 != 0;
+    ops.tmp32 = W.tmp32.p;
+    st = fp64_solve(A, ops, W, perm_dev, opts, x0, rho_dev, info, s);
+    W.release(s);
+    return st;
+}
+
+extern "C" om_status om_steady_state_solve_nojump(const om_matrix *A, const om_nojump *M, const om_solve_opts *opts,
+                                                  const double *x0, double *rho_dev, om_solve_info *info,
+                                                  void *stream) {
+    if (opts && opts->precision == 1) return solve_mixed_nojump(A, M, opts, x0, rho_dev, info, stream);
+    cudaStream_t s = as_stream(stream);
+    GmresWork<double2> W;
+    om_status st = guarded([&] {
+        check_nojump_args(A, M, opts);
+        OM_REQUIRE(rho_dev, "rho_dev is NULL");
+        W.alloc(A->N, opts->restart, s);
+    });
+    if (st != OM_OK) {
+        W.release(s);
+        return st;
+    }
+    NojumpOps ops;
+    ops.A = A;
+    ops.M = M;
+    st = fp64_solve(A, ops, W, nullptr, opts, x0, rho_dev, info, s);
+    W.release(s);
+    return st;
 }
 
 extern "C" om_status om_ilu_apply(const om_ilu *M, int32_t flags, const double *v, double *z, void *stream) {
