@@ -22,8 +22,8 @@ its inverse out from that definition:
 * ``nojump_operator`` -- S as a sparse matrix (Kronecker products);
 * ``NoJumpInverse`` / ``nojump_solve`` -- X with K X + X K^dag = Y (a
   Sylvester equation, solved by the Bartels-Stewart method: complex Schur form
-  of K, then a triangular Sylvester solve), or with K^dag X + X K = Y for the
-  adjoint S^H;
+  of K, then a triangular Sylvester solve by block recursion,
+  ``triangular_sylvester``), or with K^dag X + X K = Y for the adjoint S^H;
 * ``nojump_solve_dense`` -- the same by dense LU of S (tiny sizes only);
 * ``steady_state_nojump`` -- GMRES on L~ (Eq. 5) right-preconditioned by
   S^{-1}; its answer is the steady state of Eq. 5 whatever the
@@ -73,11 +73,39 @@ def jump_operator(p: Params, nth_floor: float = 1e-15) -> sp.csr_matrix:
     return J
 
 
+def triangular_sylvester(T1: np.ndarray, T2: np.ndarray, Y: np.ndarray, base: int = 256) -> np.ndarray:
+    """X with T1 X + X T2^dag = Y for upper triangular T1 (m x m), T2 (n x n).
+
+    Block recursion (the Bartels-Stewart back substitution by blocks): with
+    T1 = [[A, B], [0, C]] the bottom block row solves C X2 + X2 T2^dag = Y2 and
+    then A X1 + X1 T2^dag = Y1 - B X2; with T2 = [[D, E], [0, F]] the right
+    block column solves T1 X2 + X2 F^dag = Y2 and then T1 X1 + X1 D^dag =
+    Y1 - X2 E^dag.  Blocks of at most `base` rows and columns go to LAPACK's
+    ztrsyl."""
+    m, n = Y.shape
+    if m <= base and n <= base:
+        X, scale, info = sla.lapack.ztrsyl(T1, T2, Y, trana="N", tranb="C", isgn=1)
+        if info < 0:
+            raise ValueError(f"ztrsyl argument {-info}")
+        return X / scale
+    if m >= n:
+        h = m // 2
+        X2 = triangular_sylvester(T1[h:, h:], T2, Y[h:], base)
+        X1 = triangular_sylvester(T1[:h, :h], T2, Y[:h] - T1[:h, h:] @ X2, base)
+        return np.vstack([X1, X2])
+    h = n // 2
+    X2 = triangular_sylvester(T1, T2[h:, h:], Y[:, h:], base)
+    X1 = triangular_sylvester(T1, T2[:h, :h], Y[:, :h] - X2 @ T2[:h, h:].conj().T, base)
+    return np.hstack([X1, X2])
+
+
 class NoJumpInverse:
     """S^{-1} and S^{-H} by the Bartels-Stewart method: the complex Schur form
     K = Q T Q^dag is computed once; then K X + X K^dag = Y becomes
-    T X' + X' T^dag = Q^dag Y Q (a triangular Sylvester equation, LAPACK
-    ztrsyl) with X = Q X' Q^dag."""
+    T X' + X' T^dag = Q^dag Y Q (a triangular Sylvester equation, solved by
+    ``triangular_sylvester``) with X = Q X' Q^dag.  The adjoint
+    K^dag X + X K = Y becomes T^dag X' + X' T = Q^dag Y Q, brought to the same
+    upper triangular form by reversing the order of rows and columns."""
 
     def __init__(self, p: Params, nth_floor: float = 1e-15, K: np.ndarray | None = None):
         self.n = p.Nc * p.Nm
@@ -88,12 +116,14 @@ class NoJumpInverse:
         n, T, Q = self.n, self.T, self.Q
         Y = np.asarray(y, dtype=np.complex128).reshape((n, n), order="F")
         Yh = Q.conj().T @ Y @ Q
-        # forward: T X' + X' T^dag = Yh;  adjoint (K^dag X + X K = Y): T^dag X' + X' T = Yh
-        trana, tranb = ("C", "N") if adjoint else ("N", "C")
-        Xh, scale, info = sla.lapack.ztrsyl(T, T, Yh, trana=trana, tranb=tranb, isgn=1)
-        if info < 0:
-            raise ValueError(f"ztrsyl argument {-info}")
-        X = Q @ (Xh / scale) @ Q.conj().T
+        if adjoint:
+            # J (reversal) turns T^dag into the upper triangular U = J T^dag J,
+            # and J T J = U^dag:  U X'' + X'' U^dag = J Yh J,  X' = J X'' J
+            U = T.conj().T[::-1, ::-1]
+            Xh = triangular_sylvester(U, U, Yh[::-1, ::-1])[::-1, ::-1]
+        else:
+            Xh = triangular_sylvester(T, T, Yh)
+        X = Q @ Xh @ Q.conj().T
         return X.reshape(-1, order="F")
 
 

@@ -104,3 +104,21 @@ def test_nojump_preconditioned_gmres_gives_the_steady_state(mode):
     ref = steady_state_dense(p, mode)
     assert ok
     assert np.abs(x - ref.x).max() <= 1e-11
+
+
+@pytest.mark.parametrize("m,n", [(37, 37), (300, 300), (300, 170), (90, 410)])
+def test_block_recursion_matches_lapack(m, n):
+    """The block recursion of the triangular Sylvester solve against LAPACK's
+    unblocked ztrsyl on the whole system, and by its residual."""
+    import scipy.linalg as sla
+
+    from oracle.nojump import triangular_sylvester
+
+    rng = np.random.default_rng(m * 1000 + n)
+    T1 = np.triu(rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))) + np.diag(-2.0 + 1j * np.arange(m))
+    T2 = np.triu(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) + np.diag(-1.5 - 0.5j * np.arange(n))
+    Y = rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n))
+    X = triangular_sylvester(T1, T2, Y, base=32)
+    R, scale, info = sla.lapack.ztrsyl(T1, T2, Y, trana="N", tranb="C", isgn=1)
+    np.testing.assert_allclose(X, R / scale, rtol=1e-9, atol=1e-12 * np.abs(R).max())
+    assert np.abs(T1 @ X + X @ T2.conj().T - Y).max() <= 1e-10 * np.abs(Y).max()
