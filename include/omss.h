@@ -260,6 +260,13 @@ void om_nojump_free(om_nojump *M);
 /* ---- single kernels, exposed for parity tests -------------------------------
  * y = A x (DEVICE c128 vectors of length nrows). */
 om_status om_spmv(const om_matrix *A, const double *x, double *y, void *stream);
+/* y = L~ x for an UNPERMUTED matrix of om_build_liouvillian, computed from the
+ * closed-form stencil of Eq. 3 (at most 13 terms per row, coefficients from
+ * per-level tables) and the trace row of Eq. 5 instead of the stored CSR
+ * values: the operator of the no-jump solves.  DEVICE c128 vectors of N
+ * entries, x and y must not alias.  Errors: OM_EINVAL (NULL, aliasing or a
+ * permuted matrix), OM_ECUDA. */
+om_status om_liouvillian_apply(const om_matrix *A, const double *x, double *y, void *stream);
 /* z = (L U)^{-1} v, or (L U)^{-H} v, with DEVICE c128[N] vectors (z and v may
  * alias).  flags bit 0: sweep with the complex128 data (the factor must have
  * been built with it), else complex64; bit 1: apply the conjugate transpose
@@ -283,13 +290,13 @@ om_status om_ilu_condest(const om_ilu *M, int32_t flags, double *out, void *stre
  * computes the same z as om_ilu_apply with flag bit 2 (one-block sweeps; same
  * flags otherwise, same DEVICE c128 vectors,
  * z and v may alias) but takes its scratch -- a complex64 work vector of at
- * most 1,048,576 rows and a status word -- from a static device array that
- * every GPU loading the library holds (8 MiB) until the process exits, and
- * calls no allocator.  Factors with more rows are rejected with OM_EINVAL.
- * The first call on each device looks up the array's device address (with
- * that device current); make it before any stream capture.  All calls share
- * the array: calls whose work overlaps on the GPU race.  Errors: OM_EINVAL,
- * OM_ECUDA. */
+ * most 1,048,576 rows -- from a static device array that every GPU loading
+ * the library holds (8 MiB) until the process exits, and calls no allocator.
+ * Factors with more rows are rejected with OM_EINVAL.  The first call on each
+ * device looks up the array's device address (with that device current).
+ * Every call synchronises its stream before returning.  All calls share the
+ * array: calls whose work overlaps on the GPU (two host threads on two
+ * streams, say) race.  Errors: OM_EINVAL, OM_ECUDA. */
 om_status om_ilu_apply_noalloc(const om_ilu *M, int32_t flags, const double *v, double *z,
                                void *stream);
 /* <a^dag a>, <b^dag b> of a DEVICE rho (c128 n x n column-major); out HOST double[2]. */
@@ -300,8 +307,9 @@ om_status om_observables(int32_t Nc, int32_t Nm, const double *rho_dev, double o
  * om_kernel_launches: number of kernels the library has launched since it was
  * loaded.  om_profile(1) starts recording CUDA events around every one-block
  * triangular sweep (category 0), SpMV (category 1), split sweep over all
- * SMs (category 2) and no-jump preconditioner application (category 3: its
- * four products) launch, om_profile(0) stops, both
+ * SMs (category 2), no-jump preconditioner application (category 3: its
+ * four products), Gram-Schmidt step of GMRES (category 4: the two CGS2 passes)
+ * and stencil application of L~ (category 5) launch, om_profile(0) stops, both
  * discard earlier records; om_profile_read returns the summed device time
  * (milliseconds, HOST out) and launch count of a category, synchronising on
  * the recorded events. */

@@ -63,6 +63,7 @@ SIGNATURES = {
                                                c_vp]),
     "om_nojump_free": (None, [c_vp]),
     "om_spmv": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
+    "om_liouvillian_apply": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
     "om_ilu_apply": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp]),
     "om_ilu_apply_noalloc": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp]),
     "om_ilu_condest": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_dbl), c_vp]),

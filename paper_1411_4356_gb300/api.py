@@ -302,6 +302,15 @@ def spmv(A: Matrix, x: torch.Tensor, stream=None) -> torch.Tensor:
     return y
 
 
+def liouvillian_apply(A: Matrix, x: torch.Tensor, stream=None) -> torch.Tensor:
+    """y = L~ x from the stencil of Eq. 3 (unpermuted matrices only)."""
+    _require_cuda(x, torch.complex128, A.N, "x")
+    y = torch.empty_like(x)
+    check(_lib.load().om_liouvillian_apply(A.handle, _ptr(x), _ptr(y), ctypes.c_void_p(_stream(stream))),
+          "om_liouvillian_apply")
+    return y
+
+
 def ilu_apply(M: ILU, v: torch.Tensor, conj_transpose: bool = False, fp64: bool = False,
               single_block: bool = False, stream=None) -> torch.Tensor:
     """z = (L U)^{-1} v (or (L U)^{-H} v); fp64 selects the complex128 sweeps,
@@ -336,7 +345,7 @@ def kernel_launches() -> int:
     return int(_lib.load().om_kernel_launches())
 
 
-PROF_SWEEP, PROF_SPMV, PROF_SPLIT, PROF_NOJUMP = 0, 1, 2, 3
+PROF_SWEEP, PROF_SPMV, PROF_SPLIT, PROF_NOJUMP, PROF_KRYLOV, PROF_STENCIL = 0, 1, 2, 3, 4, 5
 
 
 def profile(enable: bool) -> None:

@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cmath>
 #include <memory>
+#include <vector>
 
 #include "common.cuh"
 #include "scan.cuh"
@@ -128,7 +129,176 @@ __global__ void diag_positions(int32_t n, int32_t *pos) {
     if (i < n) pos[i] = (int32_t)((int64_t)i * (n + 1));
 }
 
+// ---------------------------------------------------------------- stencil
+// y = L~ x from the coefficients of liouvillian_row, with the square roots and
+// the per-level terms read from tables indexed by the Hilbert index (one
+// entry per level: FP64 on GB300 runs at a small fraction of FP32, so no
+// coefficient is recomputed with a square root per row).  Row k = i + j n:
+//   y_k = -i sum_l (H_il x_lj - x_il H_lj) + jumps + diagonal,
+// the imaginary couplings applied as i b x = (-b x.y, b x.x), the real jump
+// couplings as a x.  Row 0 (the trace row) is written by trace_row_apply.
+enum { S_HD = 0, S_DR, S_GM, S_GP, S_EM, S_EP, S_SM, S_SP, S_SC1, S_COUNT };
+
+template <class R>
+struct StencilArgs {
+    const R *t;            // S_COUNT tables of n entries
+    const int32_t *cm;     // (c << 16) | m per Hilbert index
+    int32_t n, Nm;
+    int64_t N;
+    R kappa, gam_down, gam_up, w;
+    int32_t trace_mode;
+};
+
+template <class T>
+struct CxOps;
+template <>
+struct CxOps<double2> {
+    using R = double;
+};
+template <>
+struct CxOps<float2> {
+    using R = float;
+};
+
+// sum over the entries of row k >= 0 of L (no trace row)
+template <class T, class R>
+__device__ inline T stencil_row(const StencilArgs<R> &a, int32_t k, const T *__restrict__ x) {
+    const int32_t n = a.n, Nm = a.Nm;
+    const int32_t i = k % n, j = k / n;
+    const int32_t pi = __ldg(a.cm + i), pj = __ldg(a.cm + j);
+    const int32_t ci = pi >> 16, mi = pi & 0xFFFF, cj = pj >> 16, mj = pj & 0xFFFF;
+    const R *t = a.t;
+    auto tab = [&](int which, int32_t h) { return __ldg(t + (int64_t)which * n + h); };
+    R yr = 0, yi = 0;
+    auto real_c = [&](R c, T v) {
+        yr = fma(c, v.x, yr);
+        yi = fma(c, v.y, yi);
+    };
+    auto imag_c = [&](R b, T v) {  // (i b) v
+        yr = fma(-b, v.y, yr);
+        yi = fma(b, v.x, yi);
+    };
+    // diagonal
+    {
+        const R re = (R)-0.5 * (tab(S_DR, i) + tab(S_DR, j));
+        const R im = -(tab(S_HD, i) - tab(S_HD, j));
+        const T v = x[k];
+        yr = fma(re, v.x, fma(-im, v.y, yr));
+        yi = fma(re, v.y, fma(im, v.x, yi));
+    }
+    // left term -i H_il x_lj: l = i -/+ 1 (g0 c sqrt), l = i -/+ N_m (E sqrt)
+    if (mi >= 1) imag_c(-tab(S_GM, i), x[k - 1]);
+    if (mi + 1 < Nm) imag_c(-tab(S_GP, i), x[k + 1]);
+    if (ci >= 1) imag_c(-tab(S_EM, i), x[k - Nm]);
+    if (i + Nm < n) imag_c(-tab(S_EP, i), x[k + Nm]);
+    // right term +i x_il H_lj: l = j -/+ 1, j -/+ N_m
+    if (mj >= 1) imag_c(tab(S_GM, j), x[k - n]);
+    if (mj + 1 < Nm) imag_c(tab(S_GP, j), x[k + n]);
+    if (cj >= 1) imag_c(tab(S_EM, j), x[k - (int64_t)Nm * n]);
+    if (j + Nm < n) imag_c(tab(S_EP, j), x[k + (int64_t)Nm * n]);
+    // jumps: b^dag rho b -> x_{i-1, j-1}; b rho b^dag -> x_{i+1, j+1}; a rho a^dag -> x_{i+N_m, j+N_m}
+    if (mi >= 1 && mj >= 1) real_c(a.gam_up * tab(S_SM, i) * tab(S_SM, j), x[k - 1 - n]);
+    if (mi + 1 < Nm && mj + 1 < Nm) real_c(a.gam_down * tab(S_SP, i) * tab(S_SP, j), x[k + 1 + n]);
+    if (i + Nm < n && j + Nm < n) real_c(a.kappa * tab(S_SC1, i) * tab(S_SC1, j), x[k + Nm + (int64_t)Nm * n]);
+    T out;
+    out.x = yr;
+    out.y = yi;
+    return out;
+}
+
+template <class T, class R>
+__global__ void __launch_bounds__(256) stencil_apply(StencilArgs<R> a, const T *__restrict__ x, T *__restrict__ y) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x + 1; k < a.N; k += stride)
+        y[k] = stencil_row<T, R>(a, (int32_t)k, x);
+}
+
+// y_0: w Tr(x) (replace mode) or (row 0 of L) x + w Tr(x) (add mode), one
+// block, fixed summation order
+template <class T, class R>
+__global__ void trace_row_apply(StencilArgs<R> a, const T *__restrict__ x, T *__restrict__ y) {
+    __shared__ R sr[256], si[256];
+    R tr = 0, ti = 0;
+    for (int32_t h = threadIdx.x; h < a.n; h += blockDim.x) {
+        const T v = x[(int64_t)h * (a.n + 1)];
+        tr += v.x;
+        ti += v.y;
+    }
+    sr[threadIdx.x] = tr;
+    si[threadIdx.x] = ti;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        R s0 = 0, s1 = 0;
+        for (int q = 0; q < (int)blockDim.x; ++q) {
+            s0 += sr[q];
+            s1 += si[q];
+        }
+        T out;
+        out.x = a.w * s0;
+        out.y = a.w * s1;
+        if (a.trace_mode == 1) {
+            const T r = stencil_row<T, R>(a, 0, x);
+            out.x += r.x;
+            out.y += r.y;
+        }
+        y[0] = out;
+    }
+}
+
+template <class T, class R>
+void launch_stencil(const om_matrix &A, const R *tab, const T *x, T *y, cudaStream_t s) {
+    OM_REQUIRE(!A.permuted && tab && A.hcm.p, "the stencil operator needs the unpermuted matrix of om_build_liouvillian");
+    const double Gm = A.params.omega_m / A.params.Q_m;
+    StencilArgs<R> a;
+    a.t = tab;
+    a.cm = A.hcm.p;
+    a.n = A.n;
+    a.Nm = A.params.Nm;
+    a.N = A.N;
+    a.kappa = (R)A.params.kappa;
+    a.gam_down = (R)(Gm * (1.0 + A.nth_eff));
+    a.gam_up = (R)(Gm * A.nth_eff);
+    a.w = (R)A.w;
+    a.trace_mode = A.trace_mode;
+    const int64_t need = (A.N + 255) / 256;
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 16));
+    ProfScope prof(PROF_STENCIL, s);
+    stencil_apply<T, R><<<blocks, 256, 0, s>>>(a, x, y);
+    note_launch();
+    trace_row_apply<T, R><<<1, 256, 0, s>>>(a, x, y);
+    note_launch();
+    OM_CHECK_LAUNCH();
+}
+
+// the tables of StencilArgs for the parameters of a matrix (host)
+void build_stencil_tables(const Model &M, std::vector<double> &t, std::vector<int32_t> &cm) {
+    const int n = M.n;
+    t.assign((size_t)S_COUNT * n, 0.0);
+    cm.resize(n);
+    for (int h = 0; h < n; ++h) {
+        const int c = h / M.Nm, m = h % M.Nm;
+        cm[h] = (c << 16) | m;
+        t[(size_t)S_HD * n + h] = h_diag(M, c, m);
+        t[(size_t)S_DR * n + h] = M.kappa * c + M.gam_down * m + M.gam_up * bbdag(M, m);
+        t[(size_t)S_GM * n + h] = M.g0 * c * std::sqrt((double)m);
+        t[(size_t)S_GP * n + h] = M.g0 * c * std::sqrt((double)(m + 1));
+        t[(size_t)S_EM * n + h] = M.E * std::sqrt((double)c);
+        t[(size_t)S_EP * n + h] = M.E * std::sqrt((double)(c + 1));
+        t[(size_t)S_SM * n + h] = std::sqrt((double)m);
+        t[(size_t)S_SP * n + h] = std::sqrt((double)(m + 1));
+        t[(size_t)S_SC1 * n + h] = std::sqrt((double)(c + 1));
+    }
+}
+
 }  // namespace
+
+void liouvillian_apply_c128(const om_matrix &A, const double2 *x, double2 *y, cudaStream_t s) {
+    launch_stencil<double2, double>(A, A.stab.p, x, y, s);
+}
+void liouvillian_apply_c64(const om_matrix &A, const float2 *x, float2 *y, cudaStream_t s) {
+    launch_stencil<float2, float>(A, A.stab32.p, x, y, s);
+}
+
 }  // namespace omss
 
 using namespace omss;
@@ -141,6 +311,9 @@ om_matrix::~om_matrix() {
     d_row0_col.release(s);
     d_row0_val.release(s);
     diag_pos.release(s);
+    stab.release(s);
+    stab32.release(s);
+    hcm.release(s);
     val32.release(s);
     h_rowptr.release(s);
     h_col.release(s);
@@ -261,6 +434,19 @@ extern "C" om_status om_build_liouvillian(const om_params *params, const om_buil
                                     cudaMemcpyHostToDevice, s));
         OM_CUDA_TRY(cudaMemcpyAsync(A->d_row0_val.p, A->row0_val.data(), sizeof(double2) * cnt0,
                                     cudaMemcpyHostToDevice, s));
+        {  // stencil tables
+            std::vector<double> t;
+            std::vector<int32_t> cm;
+            build_stencil_tables(M, t, cm);
+            std::vector<float> t32(t.begin(), t.end());
+            A->stab.alloc(t.size(), s);
+            A->stab32.alloc(t32.size(), s);
+            A->hcm.alloc(cm.size(), s);
+            OM_CUDA_TRY(cudaMemcpyAsync(A->stab.p, t.data(), sizeof(double) * t.size(), cudaMemcpyHostToDevice, s));
+            OM_CUDA_TRY(cudaMemcpyAsync(A->stab32.p, t32.data(), sizeof(float) * t32.size(), cudaMemcpyHostToDevice, s));
+            OM_CUDA_TRY(cudaMemcpyAsync(A->hcm.p, cm.data(), sizeof(int32_t) * cm.size(), cudaMemcpyHostToDevice, s));
+            OM_CUDA_TRY(cudaStreamSynchronize(s));
+        }
         A->diag_pos.alloc(n, s);
         diag_positions<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((int32_t)n, A->diag_pos.p); omss::note_launch();
         OM_CHECK_LAUNCH();
@@ -269,5 +455,14 @@ extern "C" om_status om_build_liouvillian(const om_params *params, const om_buil
         normbits.release(s);
         OM_CUDA_TRY(cudaStreamSynchronize(s));  // host vectors above go out of scope
         *out = A.release();
+    });
+}
+
+extern "C" om_status om_liouvillian_apply(const om_matrix *A, const double *x, double *y, void *stream) {
+    return guarded([&] {
+        OM_REQUIRE(A && x && y, "om_liouvillian_apply: NULL argument");
+        OM_REQUIRE(x != y, "om_liouvillian_apply: x and y must not alias");
+        liouvillian_apply_c128(*A, reinterpret_cast<const double2 *>(x), reinterpret_cast<double2 *>(y),
+                               as_stream(stream));
     });
 }

@@ -20,8 +20,11 @@ void note_launch();
 
 // Kernel timing by CUDA events, active between om_profile(1) and om_profile(0).
 // Categories: 0 = one-block triangular sweeps, 1 = SpMV, 2 = split sweeps,
-// 3 = no-jump preconditioner applications (four products each).
-enum { PROF_SWEEP = 0, PROF_SPMV = 1, PROF_SPLIT = 2, PROF_NOJUMP = 3, PROF_CATEGORIES = 4 };
+// 3 = no-jump preconditioner applications (four products each), 4 = the
+// Gram-Schmidt passes of a GMRES step (CGS2: two multi-dots and two updates),
+// 5 = stencil applications of L~.
+enum { PROF_SWEEP = 0, PROF_SPMV = 1, PROF_SPLIT = 2, PROF_NOJUMP = 3, PROF_KRYLOV = 4, PROF_STENCIL = 5,
+       PROF_CATEGORIES = 6 };
 struct ProfScope {
     int cat;
     cudaStream_t s;
@@ -147,6 +150,13 @@ struct om_matrix {
     omss::DBuf<double2> d_row0_val;
     // positions of the diagonal elements rho_ii in this matrix's numbering
     omss::DBuf<int32_t> diag_pos;
+    // per Hilbert index h = c N_m + m, the coefficients of the stencil of L
+    // (assemble.cu; unpermuted matrices only): hd, dr, g0 c sqrt(m), g0 c
+    // sqrt(m+1), E sqrt(c), E sqrt(c+1), sqrt(m), sqrt(m+1), sqrt(c+1), each n
+    // long, FP64 and FP32 copies, and (c << 16 | m)
+    omss::DBuf<double> stab;
+    omss::DBuf<float> stab32;
+    omss::DBuf<int32_t> hcm;
     // built on first use: complex64 copy of the values (mixed precision) and
     // the conjugate transpose A^H (adjoint)
     mutable omss::DBuf<float2> val32;
@@ -249,6 +259,12 @@ void nojump_apply_c128(const om_nojump &M, bool adjoint, const double2 *v, doubl
 }  // namespace omss
 
 namespace omss {
+
+// y = L~ x computed from the closed-form stencil of Eq. 3 and the trace row of
+// Eq. 5 (assemble.cu), without reading the CSR values: the operator of the
+// no-jump solves, natural order only.
+void liouvillian_apply_c128(const om_matrix &A, const double2 *x, double2 *y, cudaStream_t s);
+void liouvillian_apply_c64(const om_matrix &A, const float2 *x, float2 *y, cudaStream_t s);
 
 // Kernel launchers implemented in the .cu files.
 void spmv_c128(const int64_t *rowptr, const int32_t *col, const double2 *val, int64_t N,

@@ -13,10 +13,12 @@
 // the process exits (8 MiB).  Every call shares it and it keeps the previous
 // call's contents; nothing in it has to start at zero (each call writes the
 // whole work vector before reading it), and two calls whose work overlaps on
-// the GPU race on the same scratch.  In host code the
-// array's name is only a host-side stand-in, so the first call on each device
-// looks up its device address with cudaGetSymbolAddress (with that device
-// current) and caches it; make that first call before any stream capture.
+// the GPU race on the same scratch (for example two host threads calling it
+// on two streams).  In host code the array's name is only a host-side
+// stand-in, so the first call on each device looks up its device address
+// with cudaGetSymbolAddress (with that device current) and caches it.  Every
+// call ends by synchronising its stream, so a call returns with its result
+// written.
 #include <mutex>
 #include <vector>
 

@@ -26,7 +26,7 @@ constexpr int kChunk = 8;
 
 int reduce_blocks(int64_t N) {
     int64_t need = (N + kThreads - 1) / kThreads;
-    int64_t cap = (int64_t)num_sms() * 2;
+    int64_t cap = (int64_t)num_sms() * 4;
     return (int)std::max<int64_t>(1, std::min(need, cap));
 }
 
@@ -147,6 +147,126 @@ __global__ void __launch_bounds__(kThreads) multi_axpy(const T *__restrict__ V, 
             double s = 0;
             for (int q = 0; q < kThreads / 32; ++q) s += red[q];
             norm_partial[blockIdx.x] = s;
+        }
+    }
+}
+
+// One block per contiguous range of rows: the block's share of w is held in
+// registers Q rows per thread at a time while all `count` basis vectors
+// stream past it, so w is read once per pass and each V_k once.  Per vector,
+// a warp sums its lanes with shuffles and adds the result to its own row of
+// shared memory (no block barrier in the loop); the warps are combined in a
+// fixed order at the end: partial[block * ld + k] = sum over the block's rows
+// of conj(V_k) w, k < count.
+template <class T>
+struct Rows;
+template <>
+struct Rows<double2> {
+    static constexpr int Q = 8;
+};
+template <>
+struct Rows<float2> {
+    static constexpr int Q = 16;
+};
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) multidot_rows(const T *__restrict__ V, int64_t N, int count,
+                                                          const T *__restrict__ w, int64_t rows_per_block,
+                                                          double2 *partial, int ld) {
+    using A = typename Acc<T>::A;
+    constexpr int Q = Rows<T>::Q;
+    __shared__ double2 red[kThreads / 32][128];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = lane; k < count; k += 32) red[warp][k] = make_double2(0, 0);
+    __syncwarp();
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+    const int64_t r1 = min(N, r0 + rows_per_block);
+    for (int64_t base = r0; base < r1; base += (int64_t)kThreads * Q) {
+        T wq[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int64_t i = base + threadIdx.x + (int64_t)q * kThreads;
+            wq[q] = i < r1 ? w[i] : czero<T>();
+        }
+        for (int k = 0; k < count; ++k) {
+            const T *vk = V + (int64_t)k * N;
+            T vq[Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int64_t i = base + threadIdx.x + (int64_t)q * kThreads;
+                vq[q] = i < r1 ? __ldcs(vk + i) : czero<T>();
+            }
+            A acc = czero<A>();
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                acc.x += vq[q].x * wq[q].x + vq[q].y * wq[q].y;
+                acc.y += vq[q].x * wq[q].y - vq[q].y * wq[q].x;
+            }
+            double2 sum = warp_sum(make_double2((double)acc.x, (double)acc.y));
+            if (lane == 0) red[warp][k] = cadd(red[warp][k], sum);
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < count; k += blockDim.x) {
+        double2 t = make_double2(0, 0);
+        for (int q = 0; q < kThreads / 32; ++q) t = cadd(t, red[q][k]);
+        partial[(int64_t)blockIdx.x * ld + k] = t;
+    }
+}
+
+// w -= sum_{k < count} h[k] V_k over the block's rows, Q rows per thread at a
+// time; optionally the block's partial sum of |w|^2
+template <class T>
+__global__ void __launch_bounds__(kThreads) multi_axpy_rows(const T *__restrict__ V, int64_t N, int count,
+                                                            const double2 *__restrict__ h, T *w,
+                                                            int64_t rows_per_block, double *norm_partial) {
+    using S = typename Acc<T>::S;
+    constexpr int Q = Rows<T>::Q / 2;
+    __shared__ T hs[128];
+    __shared__ double red[kThreads / 32];
+    for (int k = threadIdx.x; k < count; k += blockDim.x) hs[k] = narrow_to<T>(h[k]);
+    __syncthreads();
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+    const int64_t r1 = min(N, r0 + rows_per_block);
+    S nrm = 0;
+    for (int64_t base = r0; base < r1; base += (int64_t)kThreads * Q) {
+        T wq[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int64_t i = base + threadIdx.x + (int64_t)q * kThreads;
+            wq[q] = i < r1 ? w[i] : czero<T>();
+        }
+        for (int k = 0; k < count; ++k) {
+            const T *vk = V + (int64_t)k * N;
+            const T hk = hs[k];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int64_t i = base + threadIdx.x + (int64_t)q * kThreads;
+                if (i < r1) {
+                    const T v = __ldcs(vk + i);
+                    wq[q].x -= hk.x * v.x - hk.y * v.y;
+                    wq[q].y -= hk.x * v.y + hk.y * v.x;
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int64_t i = base + threadIdx.x + (int64_t)q * kThreads;
+            if (i < r1) {
+                w[i] = wq[q];
+                nrm += wq[q].x * wq[q].x + wq[q].y * wq[q].y;
+            }
+        }
+    }
+    if (norm_partial) {
+        double d = (double)nrm;
+        for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0;
+            for (int q = 0; q < kThreads / 32; ++q) t += red[q];
+            norm_partial[blockIdx.x] = t;
         }
     }
 }
@@ -390,6 +510,7 @@ GmresResult gmres_cycle(KrylovOps<T> &ops, const T *b, T *x, double target, int 
     const int64_t N = W.N;
     const int m = W.m;
     const int nb = reduce_blocks(N);
+    const int64_t rpb = (N + nb - 1) / nb;  // rows per block of the CGS2 kernels
     const int ld = m + 2;
     double *d_est = W.scal.p + 0;
     double *d_nrm = W.scal.p + 1;
@@ -421,26 +542,26 @@ GmresResult gmres_cycle(KrylovOps<T> &ops, const T *b, T *x, double target, int 
         ops.precond(vj, zj, s);
         ops.apply(zj, W.w.p, s);
         // CGS2: h1 = V^H w, w -= V h1; h2 = V^H w, w -= V h2; h = h1 + h2
-        for (int pass = 0; pass < 2; ++pass) {
-            for (int f = 0; f <= j; f += kChunk) {
-                int cnt = std::min(kChunk, j + 1 - f);
-                multidot<T><<<nb, kThreads, 0, s>>>(W.V.p, N, f, cnt, W.w.p, W.partial.p, ld);
+        {
+            ProfScope prof(PROF_KRYLOV, s);
+            for (int pass = 0; pass < 2; ++pass) {
+                multidot_rows<T><<<nb, kThreads, 0, s>>>(W.V.p, N, j + 1, W.w.p, rpb, W.partial.p, ld);
                 omss::note_launch();
+                finish_dots<<<1, 128, 0, s>>>(W.partial.p, nb, j + 1, ld, W.h.p, pass);
+                omss::note_launch();
+                if (pass == 0) {
+                    multi_axpy_rows<T><<<nb, kThreads, 0, s>>>(W.V.p, N, j + 1, W.h.p, W.w.p, rpb, nullptr);
+                    omss::note_launch();
+                } else {
+                    finish_dots<<<1, 128, 0, s>>>(W.partial.p, nb, j + 1, ld, W.y2.p, 0);
+                    omss::note_launch();
+                    multi_axpy_rows<T><<<nb, kThreads, 0, s>>>(W.V.p, N, j + 1, W.y2.p, W.w.p, rpb, W.scal.p + 8);
+                    omss::note_launch();
+                    finish_norm<<<1, 32, 0, s>>>(W.scal.p + 8, nb, d_nrm);
+                    omss::note_launch();
+                }
+                OM_CHECK_LAUNCH();
             }
-            finish_dots<<<1, 128, 0, s>>>(W.partial.p, nb, j + 1, ld, W.h.p, pass);
-            omss::note_launch();
-            if (pass == 0) {
-                multi_axpy<T><<<nb, kThreads, 0, s>>>(W.V.p, N, j + 1, W.h.p, W.w.p, nullptr);
-                omss::note_launch();
-            } else {
-                finish_dots<<<1, 128, 0, s>>>(W.partial.p, nb, j + 1, ld, W.y2.p, 0);
-                omss::note_launch();
-                multi_axpy<T><<<nb, kThreads, 0, s>>>(W.V.p, N, j + 1, W.y2.p, W.w.p, W.scal.p + 8);
-                omss::note_launch();
-                finish_norm<<<1, 32, 0, s>>>(W.scal.p + 8, nb, d_nrm);
-                omss::note_launch();
-            }
-            OM_CHECK_LAUNCH();
         }
         scale_into<T><<<grid_for(N), kThreads, 0, s>>>(W.w.p, d_nrm, N, vnext);
         omss::note_launch();

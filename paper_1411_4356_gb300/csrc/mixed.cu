@@ -64,13 +64,12 @@ struct InnerOps : KrylovOps<float2> {
     }
 };
 
-// complex64 inner solve with the no-jump preconditioner (natural order)
+// complex64 inner solve with the no-jump preconditioner (natural order); the
+// operator is applied from its stencil in FP32
 struct NojumpInnerOps : KrylovOps<float2> {
     const om_matrix *A;
     const om_nojump *M;
-    void apply(const float2 *v, float2 *out, cudaStream_t s) override {
-        spmv_c64(A->rowptr.p, A->col.p, A->val32.p, A->N, v, out, s);
-    }
+    void apply(const float2 *v, float2 *out, cudaStream_t s) override { liouvillian_apply_c64(*A, v, out, s); }
     void precond(const float2 *v, float2 *out, cudaStream_t s) override { nojump_apply_c64(*M, false, v, out, s); }
 };
 
@@ -87,13 +86,13 @@ void ensure_values_c64(const om_matrix &A, cudaStream_t s) {
 namespace {
 // the refinement loop around an inner complex64 operator/preconditioner pair
 om_status mixed_solve(const om_matrix *A, KrylovOps<float2> &ops, const int32_t *perm_dev, const om_solve_opts *opts,
-                      const double *x0, double *rho_dev, om_solve_info *info, void *stream) {
+                      const double *x0, double *rho_dev, om_solve_info *info, void *stream, bool csr_c64) {
     om_status final_status = OM_OK;
     om_status st = guarded([&] {
         auto t0 = std::chrono::steady_clock::now();
         cudaStream_t s = as_stream(stream);
         const int64_t N = A->N;
-        ensure_values_c64(*A, s);
+        if (csr_c64) ensure_values_c64(*A, s);
         GmresWork<double2> W64;
         W64.alloc(N, 1, s);
         GmresWork<float2> W32;
@@ -190,7 +189,7 @@ om_status solve_mixed(const om_matrix *A, const om_ilu *M, const int32_t *perm_d
     InnerOps ops;
     ops.A = A;
     ops.M = M;
-    return mixed_solve(A, ops, perm_dev, opts, x0, rho_dev, info, stream);
+    return mixed_solve(A, ops, perm_dev, opts, x0, rho_dev, info, stream, true);
 }
 
 void check_nojump_args(const om_matrix *A, const om_nojump *M, const om_solve_opts *o);
@@ -205,7 +204,7 @@ om_status solve_mixed_nojump(const om_matrix *A, const om_nojump *M, const om_so
     NojumpInnerOps ops;
     ops.A = A;
     ops.M = M;
-    return mixed_solve(A, ops, nullptr, opts, x0, rho_dev, info, stream);
+    return mixed_solve(A, ops, nullptr, opts, x0, rho_dev, info, stream, false);
 }
 
 }  // namespace omss

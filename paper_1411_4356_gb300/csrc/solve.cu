@@ -91,13 +91,12 @@ struct ForwardOps : KrylovOps<double2> {
     }
 };
 
-// GMRES on the unpermuted L~ with the no-jump preconditioner S^{-1}
+// GMRES on the unpermuted L~ with the no-jump preconditioner S^{-1}; the
+// operator is applied from its stencil (no CSR values streamed)
 struct NojumpOps : KrylovOps<double2> {
     const om_matrix *A;
     const om_nojump *M;
-    void apply(const double2 *v, double2 *out, cudaStream_t s) override {
-        spmv_c128(A->rowptr.p, A->col.p, A->val.p, A->N, v, out, s);
-    }
+    void apply(const double2 *v, double2 *out, cudaStream_t s) override { liouvillian_apply_c128(*A, v, out, s); }
     void precond(const double2 *v, double2 *out, cudaStream_t s) override {
         nojump_apply_c128(*M, false, v, out, s);
     }

@@ -65,3 +65,51 @@ def test_360k_rows_at_the_bench_tolerance(system):
     assert np.abs(r - r.conj().T).max() <= 1e-6
     diag = np.array(REF["diag_re"])
     assert np.abs(np.diag(r).real - diag).max() <= 1e-5
+
+
+# ------------------------------------------------------------ every entry of rho
+@pytest.fixture(scope="module")
+def oracle_full_rho():
+    """The oracle's own steady state of the 360,000-row system, every entry:
+    GMRES on L~ with its FP64 Bartels-Stewart no-jump preconditioner, to a
+    relative residual of 1e-15 (oracle/nojump.py; about a minute on the host
+    cores)."""
+    from oracle.liouvillian import Params
+    from oracle.nojump import steady_state_nojump
+
+    q = MID.params
+    p = Params(q.Nc, q.Nm, q.omega_m, q.Delta, q.kappa, q.g0, q.E, q.Q_m, q.n_th)
+    x, its, ok, _ = steady_state_nojump(p, MID.trace_mode, MID.nth_floor, restart=60, rtol=1e-15)
+    assert ok
+    n = q.Nc * q.Nm
+    return x.reshape((n, n), order="F")
+
+
+def test_oracle_references_agree(oracle_full_rho):
+    """The two oracle routes (RCM + ILUT GMRES, stored; no-jump GMRES, computed
+    here) give the same steady state."""
+    diag = np.array(REF["diag_re"]) + 1j * np.array(REF["diag_im"])
+    assert np.abs(np.diag(oracle_full_rho) - diag).max() <= 1e-11
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-12), (0, 1e-11)])
+def test_360k_every_entry_no_jump_path(oracle_full_rho, precision, tol):
+    """All 360,000 entries of rho from the no-jump path against the oracle, at
+    the bench's tolerance (1e-12) and at the loosest FP64 one that still meets
+    1e-9 (1e-11; at 1e-10 the error measured 5.9e-9)."""
+    A = api.build_liouvillian(MID.params, MID.trace_mode, MID.nth_floor)
+    M = api.nojump_factor(MID.params, nth_floor=MID.nth_floor, eig32=True)
+    rho, info = api.steady_state_solve_nojump(A, M, restart=50, tol=tol, precision=precision)
+    assert info.status == 0 and info.eta <= tol
+    err = np.abs(rho.cpu().numpy() - oracle_full_rho).max()
+    print(f"precision {precision} tol {tol:.0e}: {info.iterations} iterations, eta {info.eta:.1e}, max err {err:.1e}")
+    assert err <= 1e-9
+
+
+def test_360k_every_entry_ilu_path(system, oracle_full_rho):
+    """All entries of rho from the paper's RCM + ILUT path (eta <= 1e-15)."""
+    Ar, M, perm = system
+    rho, info = api.steady_state_solve(Ar, M, perm, restart=MID.restart, tol=1e-15, max_iters=3000,
+                                       raise_on_noconv=False)
+    assert info.status == 0
+    assert np.abs(rho.cpu().numpy() - oracle_full_rho).max() <= 1e-9

@@ -132,3 +132,23 @@ def test_permuted_matrix_is_rejected():
     M = api.nojump_factor(p)
     with pytest.raises(OMError):
         api.steady_state_solve_nojump(Ar, M)
+
+
+@pytest.mark.parametrize("Nc,Nm", [(1, 1), (1, 5), (2, 1), (3, 5), (4, 10), (6, 20)])
+@pytest.mark.parametrize("mode", ["replace", "add"])
+def test_stencil_operator_matches_oracle(Nc, Nm, mode):
+    """y = L~ x from the stencil against the oracle's assembled L~ (Kronecker
+    products) and against the library's CSR SpMV, including n_th = 0 floored."""
+    from oracle.liouvillian import augmented
+
+    for kw in (BASE, {**BASE, "n_th": 0.0}):
+        p = SystemParams(Nc, Nm, **kw)
+        A = api.build_liouvillian(p, mode)
+        x = rand_vec(p.N, Nc * 7 + Nm)
+        xt = torch.from_numpy(x).cuda()
+        y = api.liouvillian_apply(A, xt).cpu().numpy()
+        Lt, *_ = augmented(oparams(p), mode, 1e-15)
+        ref = Lt @ x
+        scale = np.abs(Lt).sum(axis=1).max() * np.abs(x).max()
+        assert np.abs(y - ref).max() <= 1e-14 * scale
+        assert np.abs(y - api.spmv(A, xt).cpu().numpy()).max() <= 1e-14 * scale

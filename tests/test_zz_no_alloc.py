@@ -49,6 +49,27 @@ def test_noalloc_matches_ilu_apply(Nc, Nm, d, fill):
             np.testing.assert_allclose(zz, r, rtol=0, atol=1e-12 * np.abs(r).max())
 
 
+def test_noalloc_after_a_larger_call():
+    """A call on a 14,400-row factor, then one on a 1,600-row factor: the
+    second must not see what the first left in the shared scratch beyond its
+    own rows."""
+    rng = np.random.default_rng(5)
+    for (Nc, Nm, d, fill) in [(6, 20, 1e-4, 20.0), (4, 10, 1e-4, 10.0)]:
+        p = SystemParams(Nc, Nm, **BASE)
+        A = api.build_liouvillian(p)
+        Ar, perm = api.permute(A)
+        M = api.ilu_factor(Ar, d, fill, adjoint=True)
+        for flags in (0, 2):
+            v = torch.from_numpy(rng.standard_normal(Ar.N) + 1j * rng.standard_normal(Ar.N)).cuda()
+            ref = torch.empty_like(v)
+            assert call("om_ilu_apply", M, flags | 4, v, ref) == 0
+            z = torch.full_like(v, complex("nan"))
+            assert call("om_ilu_apply_noalloc", M, flags, v, z) == 0, _lib.load().om_last_error()
+            torch.cuda.synchronize()
+            r, zz = ref.cpu().numpy(), z.cpu().numpy()
+            np.testing.assert_allclose(zz, r, rtol=0, atol=1e-12 * np.abs(r).max())
+
+
 def test_noalloc_rejects_oversized_factor():
     p = SystemParams(10, 110, **BASE)  # 1,210,000 rows > 1,048,576
     A = api.build_liouvillian(p)
