@@ -7,7 +7,10 @@ system's parameters), permutes it, factors it (d = 1e-5, p = 100) and runs
 the complex64 preconditioner solve three times; `spmv_10x60` runs the SpMV
 three times instead.  Inputs are larger than L2 (the factors are ~0.4 GB).
 `batched_16` solves the first 16 draws of the 512-system sweep with the
-lock-step batched engine.
+lock-step batched engine.  `nojump_20x100` factors K of the 4,000,000-row
+system (N_c = 20, N_m = 100, the 16M-row system's parameters) and applies the
+no-jump preconditioner three times with the TF32 tensor-core products (each
+expanded operand 64 MB, each data matrix 32 MB: larger than L2 together).
 """
 from __future__ import annotations
 
@@ -61,7 +64,20 @@ def batched(count=16):
     print(f"batched case: {count} systems, iterations {[i.iterations for i in infos]}")
 
 
-CASES = {"sweep_10x20": lambda: sweep(10, 20), "spmv_10x60": lambda: spmv(10, 60), "batched_16": batched}
+def nojump(Nc=20, Nm=100):
+    from .workloads import LARGE
+
+    p = LARGE.params.with_(Nc=Nc, Nm=Nm)
+    M = api.nojump_factor(p, nth_floor=LARGE.nth_floor, eig32=True)
+    x = torch.randn(p.N, dtype=torch.complex128, device="cuda")
+    for _ in range(3):
+        api.nojump_apply(M, x)
+    torch.cuda.synchronize()
+    print(f"nojump case: n {p.n}, rows {p.N}, tensor cores {M.tensor_cores}")
+
+
+CASES = {"sweep_10x20": lambda: sweep(10, 20), "spmv_10x60": lambda: spmv(10, 60), "batched_16": batched,
+         "nojump_20x100": lambda: nojump(20, 100)}
 
 if __name__ == "__main__":
     CASES[sys.argv[1]]()

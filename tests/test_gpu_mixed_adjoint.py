@@ -112,7 +112,9 @@ def test_adjoint_at_40000_rows_against_central_differences():
     n = p.Nc * p.Nm
     m = torch.tensor([h % p.Nm for h in range(n)], dtype=torch.float64, device="cuda")
     G = torch.diag(m.to(torch.complex128))
-    g, ainfo = api.steady_state_adjoint(Ar, M, perm, rho, G, restart=50, tol=1e-12, max_iters=5000)
+    # the adjoint's relative residual stagnates near 7e-12 here (|mu| is ~1e6 |G|:
+    # L~ is nearly singular along the slow mechanical modes), so 1e-10 is asked
+    g, ainfo = api.steady_state_adjoint(Ar, M, perm, rho, G, restart=50, tol=1e-10, max_iters=5000)
 
     def F(**kw):
         B = api.build_liouvillian(p.with_(**kw), MID.trace_mode, MID.nth_floor)

@@ -23,9 +23,9 @@ def observable(p, rho, which):
     return float((torch.diagonal(rho).real * q).sum())
 
 
-def solve(p, tol=1e-15):
+def solve(p, tol=1e-15, eig32=True):
     A = api.build_liouvillian(p, ADJOINT.trace_mode, ADJOINT.nth_floor)
-    M = api.nojump_factor(p, nth_floor=ADJOINT.nth_floor, adjoint=True, eig32=True)
+    M = api.nojump_factor(p, nth_floor=ADJOINT.nth_floor, adjoint=True, eig32=eig32)
     rho, info = api.steady_state_solve_nojump(A, M, restart=50, tol=tol, max_iters=600, raise_on_noconv=False)
     assert info.eta <= 1e-14, info
     return A, M, rho
@@ -34,11 +34,15 @@ def solve(p, tol=1e-15):
 @pytest.mark.parametrize("which", ["n_b", "n_a"])
 def test_adjoint_1440k_rows_against_central_differences(which):
     p = ADJOINT.params
-    A, M, rho = solve(p)
+    # the adjoint solve keeps a complex128 eigendecomposition (its preconditioner
+    # is then accurate to ~1e-6, against ~3e-3 from a complex64 one) and asks a
+    # relative residual of 1e-11: |mu| is large along the slow mechanical modes,
+    # so the attainable residual is near 1e-12
+    A, M, rho = solve(p, eig32=False)
     n = p.Nc * p.Nm
     h = torch.arange(n, device="cuda")
     q = ((h // p.Nm) if which == "n_a" else (h % p.Nm)).to(torch.complex128)
-    g, ainfo = api.steady_state_adjoint_nojump(A, M, rho, torch.diag(q), restart=50, tol=1e-14, max_iters=600)
+    g, ainfo = api.steady_state_adjoint_nojump(A, M, rho, torch.diag(q), restart=50, tol=1e-11, max_iters=600)
 
     def F(**kw):
         _, _, r = solve(p.with_(**kw))
