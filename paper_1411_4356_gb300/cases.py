@@ -11,6 +11,8 @@ lock-step batched engine.  `nojump_20x100` factors K of the 4,000,000-row
 system (N_c = 20, N_m = 100, the 16M-row system's parameters) and applies the
 no-jump preconditioner three times with the TF32 tensor-core products (each
 expanded operand 64 MB, each data matrix 32 MB: larger than L2 together).
+`solve_20x100` / `solve_mixed_20x100` run the whole no-jump steady-state solve
+of that system in FP64 / mixed precision (Krylov basis 3.3 GB / 1.6 GB).
 """
 from __future__ import annotations
 
@@ -76,8 +78,20 @@ def nojump(Nc=20, Nm=100):
     print(f"nojump case: n {p.n}, rows {p.N}, tensor cores {M.tensor_cores}")
 
 
+def solve(Nc=20, Nm=100, precision=0):
+    from .workloads import LARGE
+
+    p = LARGE.params.with_(Nc=Nc, Nm=Nm)
+    A = api.build_liouvillian(p, LARGE.trace_mode, LARGE.nth_floor)
+    M = api.nojump_factor(p, nth_floor=LARGE.nth_floor, eig32=True)
+    rho, info = api.steady_state_solve_nojump(A, M, restart=50, tol=1e-12, precision=precision)
+    torch.cuda.synchronize()
+    print(f"solve case: rows {p.N}, precision {precision}, iterations {info.iterations}, eta {info.eta:.2e}")
+
+
 CASES = {"sweep_10x20": lambda: sweep(10, 20), "spmv_10x60": lambda: spmv(10, 60), "batched_16": batched,
-         "nojump_20x100": lambda: nojump(20, 100)}
+         "nojump_20x100": lambda: nojump(20, 100), "solve_20x100": lambda: solve(20, 100, 0),
+         "solve_mixed_20x100": lambda: solve(20, 100, 1)}
 
 if __name__ == "__main__":
     CASES[sys.argv[1]]()

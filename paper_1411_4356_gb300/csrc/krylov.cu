@@ -65,6 +65,21 @@ __device__ inline T czero() {
     return z;
 }
 
+__device__ inline float2 warp_sum_acc(float2 v) {
+    for (int o = 16; o; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+__device__ inline double2 warp_sum_acc(double2 v) {
+    for (int o = 16; o; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+
 __device__ inline double2 warp_sum(double2 v) {
     for (int o = 16; o; o >>= 1) {
         v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
@@ -107,13 +122,15 @@ __global__ void __launch_bounds__(kThreads) multidot(const T *__restrict__ V, in
     }
 }
 
-// out[k] (+)= sum_b partial[b * ld + k], k < count, summed in block order
+// out[k] (+)= sum_b partial[b * ld + k], k < count: one warp per k (block k),
+// lane l summing the blocks l, l + 32, ... in order, then a fixed shuffle tree
 __global__ void finish_dots(const double2 *partial, int nblocks, int count, int ld, double2 *out, int accumulate) {
-    int k = threadIdx.x;
+    const int k = blockIdx.x, lane = threadIdx.x;
     if (k >= count) return;
     double2 s = make_double2(0, 0);
-    for (int b = 0; b < nblocks; ++b) s = cadd(s, partial[(int64_t)b * ld + k]);
-    out[k] = accumulate ? cadd(out[k], s) : s;
+    for (int b = lane; b < nblocks; b += 32) s = cadd(s, partial[(int64_t)b * ld + k]);
+    s = warp_sum(s);
+    if (lane == 0) out[k] = accumulate ? cadd(out[k], s) : s;
 }
 
 // w -= sum_{k < count} h[k] V_k ; optionally partial sums of |w|^2 per block
@@ -153,11 +170,12 @@ __global__ void __launch_bounds__(kThreads) multi_axpy(const T *__restrict__ V, 
 
 // One block per contiguous range of rows: the block's share of w is held in
 // registers Q rows per thread at a time while all `count` basis vectors
-// stream past it, so w is read once per pass and each V_k once.  Per vector,
-// a warp sums its lanes with shuffles and adds the result to its own row of
-// shared memory (no block barrier in the loop); the warps are combined in a
-// fixed order at the end: partial[block * ld + k] = sum over the block's rows
-// of conj(V_k) w, k < count.
+// stream past it (kVB vectors per round), so w is read once per pass and
+// each V_k once.  Per vector, a warp sums its
+// lanes with shuffles and adds the result to its own row of shared memory (no
+// block barrier in the loop); the warps are combined in a fixed order at the
+// end: partial[block * ld + k] = sum over the block's rows of conj(V_k) w,
+// k < count.
 template <class T>
 struct Rows;
 template <>
@@ -166,8 +184,9 @@ struct Rows<double2> {
 };
 template <>
 struct Rows<float2> {
-    static constexpr int Q = 16;
+    static constexpr int Q = 8;
 };
+constexpr int kVB = 1;  // basis vectors per round
 
 template <class T>
 __global__ void __launch_bounds__(kThreads) multidot_rows(const T *__restrict__ V, int64_t N, int count,
@@ -188,22 +207,33 @@ __global__ void __launch_bounds__(kThreads) multidot_rows(const T *__restrict__ 
             const int64_t i = base + threadIdx.x + (int64_t)q * kThreads;
             wq[q] = i < r1 ? w[i] : czero<T>();
         }
-        for (int k = 0; k < count; ++k) {
-            const T *vk = V + (int64_t)k * N;
-            T vq[Q];
+#pragma unroll 2
+        for (int k0 = 0; k0 < count; k0 += kVB) {
+            T vq[kVB][Q];
 #pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                const int64_t i = base + threadIdx.x + (int64_t)q * kThreads;
-                vq[q] = i < r1 ? __ldcs(vk + i) : czero<T>();
-            }
-            A acc = czero<A>();
+            for (int b = 0; b < kVB; ++b) {
+                const T *vk = V + (int64_t)(k0 + b) * N;
 #pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                acc.x += vq[q].x * wq[q].x + vq[q].y * wq[q].y;
-                acc.y += vq[q].x * wq[q].y - vq[q].y * wq[q].x;
+                for (int q = 0; q < Q; ++q) {
+                    const int64_t i = base + threadIdx.x + (int64_t)q * kThreads;
+                    vq[b][q] = (k0 + b < count && i < r1) ? __ldcs(vk + i) : czero<T>();
+                }
             }
-            double2 sum = warp_sum(make_double2((double)acc.x, (double)acc.y));
-            if (lane == 0) red[warp][k] = cadd(red[warp][k], sum);
+#pragma unroll
+            for (int b = 0; b < kVB; ++b) {
+                A acc = czero<A>();
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    acc.x += vq[b][q].x * wq[q].x + vq[b][q].y * wq[q].y;
+                    acc.y += vq[b][q].x * wq[q].y - vq[b][q].y * wq[q].x;
+                }
+                // the warp's sum in the accumulator's precision (FP32 for complex64
+                // vectors, whose terms carry FP32 rounding already); the block's
+                // running sums in FP64
+                acc = warp_sum_acc(acc);
+                if (lane == 0 && k0 + b < count)
+                    red[warp][k0 + b] = cadd(red[warp][k0 + b], make_double2((double)acc.x, (double)acc.y));
+            }
         }
     }
     __syncthreads();
@@ -214,17 +244,17 @@ __global__ void __launch_bounds__(kThreads) multidot_rows(const T *__restrict__ 
     }
 }
 
-// w -= sum_{k < count} h[k] V_k over the block's rows, Q rows per thread at a
-// time; optionally the block's partial sum of |w|^2
+// w -= sum_{k < count} h[k] V_k over the block's rows, Q rows per thread and
+// kVB vectors per round; optionally the block's partial sum of |w|^2
 template <class T>
 __global__ void __launch_bounds__(kThreads) multi_axpy_rows(const T *__restrict__ V, int64_t N, int count,
                                                             const double2 *__restrict__ h, T *w,
                                                             int64_t rows_per_block, double *norm_partial) {
     using S = typename Acc<T>::S;
-    constexpr int Q = Rows<T>::Q / 2;
+    constexpr int Q = Rows<T>::Q;
     __shared__ T hs[128];
     __shared__ double red[kThreads / 32];
-    for (int k = threadIdx.x; k < count; k += blockDim.x) hs[k] = narrow_to<T>(h[k]);
+    for (int k = threadIdx.x; k < 128; k += blockDim.x) hs[k] = k < count ? narrow_to<T>(h[k]) : czero<T>();
     __syncthreads();
     const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
     const int64_t r1 = min(N, r0 + rows_per_block);
@@ -236,16 +266,25 @@ __global__ void __launch_bounds__(kThreads) multi_axpy_rows(const T *__restrict_
             const int64_t i = base + threadIdx.x + (int64_t)q * kThreads;
             wq[q] = i < r1 ? w[i] : czero<T>();
         }
-        for (int k = 0; k < count; ++k) {
-            const T *vk = V + (int64_t)k * N;
-            const T hk = hs[k];
+#pragma unroll 2
+        for (int k0 = 0; k0 < count; k0 += kVB) {
+            T vq[kVB][Q];
 #pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                const int64_t i = base + threadIdx.x + (int64_t)q * kThreads;
-                if (i < r1) {
-                    const T v = __ldcs(vk + i);
-                    wq[q].x -= hk.x * v.x - hk.y * v.y;
-                    wq[q].y -= hk.x * v.y + hk.y * v.x;
+            for (int b = 0; b < kVB; ++b) {
+                const T *vk = V + (int64_t)(k0 + b) * N;
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const int64_t i = base + threadIdx.x + (int64_t)q * kThreads;
+                    vq[b][q] = (k0 + b < count && i < r1) ? __ldcs(vk + i) : czero<T>();
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < kVB; ++b) {
+                const T hk = hs[k0 + b];  // zero past count
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    wq[q].x -= hk.x * vq[b][q].x - hk.y * vq[b][q].y;
+                    wq[q].y -= hk.x * vq[b][q].y + hk.y * vq[b][q].x;
                 }
             }
         }
@@ -306,23 +345,29 @@ __global__ void __launch_bounds__(kThreads) vec_stats(const T *__restrict__ x, i
     }
 }
 
-// out[0] = sqrt(sum partial) (deterministic order), out[1] = sqrt(max partial)
+// out[0] = sqrt(sum partial) (deterministic order), out[1] = sqrt(max partial);
+// one warp: lane l takes the blocks l, l + 32, ..., then a fixed shuffle tree
 __global__ void finish_stats(const double *ps, const double *pm, int nblocks, double *out) {
-    if (threadIdx.x != 0) return;
     double s = 0, m = 0;
-    for (int b = 0; b < nblocks; ++b) {
+    for (int b = threadIdx.x; b < nblocks; b += 32) {
         s += ps[b];
         m = fmax(m, pm[b]);
     }
-    out[0] = sqrt(s);
-    out[1] = sqrt(m);
+    for (int o = 16; o; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sqrt(s);
+        out[1] = sqrt(m);
+    }
 }
 
 __global__ void finish_norm(const double *ps, int nblocks, double *out) {
-    if (threadIdx.x != 0) return;
     double s = 0;
-    for (int b = 0; b < nblocks; ++b) s += ps[b];
-    out[0] = sqrt(s);
+    for (int b = threadIdx.x; b < nblocks; b += 32) s += ps[b];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) out[0] = sqrt(s);
 }
 
 template <class T>
@@ -547,13 +592,13 @@ GmresResult gmres_cycle(KrylovOps<T> &ops, const T *b, T *x, double target, int 
             for (int pass = 0; pass < 2; ++pass) {
                 multidot_rows<T><<<nb, kThreads, 0, s>>>(W.V.p, N, j + 1, W.w.p, rpb, W.partial.p, ld);
                 omss::note_launch();
-                finish_dots<<<1, 128, 0, s>>>(W.partial.p, nb, j + 1, ld, W.h.p, pass);
+                finish_dots<<<j + 1, 32, 0, s>>>(W.partial.p, nb, j + 1, ld, W.h.p, pass);
                 omss::note_launch();
                 if (pass == 0) {
                     multi_axpy_rows<T><<<nb, kThreads, 0, s>>>(W.V.p, N, j + 1, W.h.p, W.w.p, rpb, nullptr);
                     omss::note_launch();
                 } else {
-                    finish_dots<<<1, 128, 0, s>>>(W.partial.p, nb, j + 1, ld, W.y2.p, 0);
+                    finish_dots<<<j + 1, 32, 0, s>>>(W.partial.p, nb, j + 1, ld, W.y2.p, 0);
                     omss::note_launch();
                     multi_axpy_rows<T><<<nb, kThreads, 0, s>>>(W.V.p, N, j + 1, W.y2.p, W.w.p, rpb, W.scal.p + 8);
                     omss::note_launch();

@@ -9,11 +9,12 @@
 // the life of the handle and are expanded once, rounded to TF32, padded with
 // zeros to 2 n_pad rows and columns (n_pad a multiple of 64).
 //
-// One CTA computes a 128 x 64 tile of C (64 complex rows x 64 columns):
-//   warp 0, lane 0: TMA producer -- 128 x 32 (A) and 64 x 32 (B) fp32 tiles,
+// One CTA computes a 128 x TN tile of C (64 complex rows x TN columns, TN =
+// 256 where that still fills the GPU with CTAs, else 64):
+//   warp 0, lane 0: TMA producer -- 128 x 32 (A) and TN x 32 (B) fp32 tiles,
 //                   128-byte swizzle, into a 4-stage ring of shared memory;
-//   warp 1, lane 0: issues tcgen05.mma.kind::tf32 (M 128, N 64, K 8) into a
-//                   128-lane x 64-column fp32 accumulator in tensor memory and
+//   warp 1, lane 0: issues tcgen05.mma.kind::tf32 (M 128, N TN, K 8) into a
+//                   128-lane x TN-column fp32 accumulator in tensor memory and
 //                   frees each stage with tcgen05.commit;
 //   all 4 warps:    read the accumulator with tcgen05.ld (warp w owns lanes
 //                   32w..32w+31), pair real and imaginary rows by a shuffle,
@@ -36,13 +37,20 @@ namespace omss {
 namespace {
 
 constexpr int TM = 128;  // expanded (real) rows per tile
-constexpr int TN = 64;   // complex columns per tile
 constexpr int TK = 32;   // fp32 per 128-byte swizzle row
 constexpr int STAGES = 4;
 constexpr int kThreads = 128;
 constexpr uint32_t A_BYTES = TM * TK * 4;
-constexpr uint32_t B_BYTES = TN * TK * 4;
-constexpr size_t SMEM_BYTES = 1024 + STAGES * (A_BYTES + B_BYTES) + 256;
+// TN complex columns per tile: 256 where the grid still fills the GPU (twice
+// the operand reuse per byte staged), else 64
+template <int TN>
+struct Tile {
+    static constexpr uint32_t B_BYTES = TN * TK * 4;
+    static constexpr size_t SMEM_BYTES = 1024 + STAGES * (A_BYTES + B_BYTES) + 256 + TN * sizeof(float2);
+    // instruction descriptor: D fp32, A and B tf32, both K-major, M = TM, N = TN
+    static constexpr uint32_t IDESC =
+        (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+};
 
 __device__ inline uint32_t s_u32(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 __device__ inline uint64_t now_ns() {
@@ -96,14 +104,11 @@ __device__ inline uint64_t smem_desc(const void *tile) {
     const uint64_t addr = s_u32(tile);
     return ((addr >> 4) & 0x3FFFull) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
 }
-// instruction descriptor: D fp32, A and B tf32, both K-major, M = TM, N = TN
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
-
-__device__ inline void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db, uint32_t accumulate) {
+__device__ inline void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t accumulate) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
-        "l"(da), "l"(db), "r"(kIdesc), "r"(accumulate)
+        "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 __device__ inline void mma_commit(uint64_t *bar) {
@@ -116,10 +121,11 @@ __device__ inline float tf32_round(float x) {
     return __uint_as_float(r);
 }
 
-template <int EPI, bool C128>
+template <int EPI, bool C128, int TN>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_product(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int n, int kt_count,
                const float2 *__restrict__ lam, void *__restrict__ out, int *status, unsigned long long limit_ns) {
+    constexpr uint32_t B_BYTES = Tile<TN>::B_BYTES;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -130,8 +136,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t *done = empty + STAGES;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    float2 *lam_s = reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(tmem_slot) + 16);  // TN entries
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * TM, j0 = blockIdx.x * TN;
+    if (EPI != 0)  // the eigenvalues of this tile's columns, for the division by D
+        for (int c = threadIdx.x; c < TN; c += kThreads) lam_s[c] = j0 + c < n ? lam[j0 + c] : make_float2(1.f, 0.f);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -176,7 +185,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint64_t da = smem_desc(sA + s * A_BYTES), db = smem_desc(sB + s * B_BYTES);
 #pragma unroll
             for (int k = 0; k < TK / 8; ++k)  // K = 8 tf32 = 32 bytes per instruction
-                mma_tf32(tmem, da + 2 * k, db + 2 * k, (kt | k) != 0 ? 1u : 0u);
+                mma_tf32(tmem, da + 2 * k, db + 2 * k, Tile<TN>::IDESC, (kt | k) != 0 ? 1u : 0u);
             mma_commit(&empty[s]);
         }
         mma_commit(done);  // arrives once every MMA issued so far has completed
@@ -192,7 +201,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool imag = (m & 1) != 0;
         float2 la = make_float2(1.f, 0.f);
         if (EPI != 0 && a < n) la = lam[a];
-#pragma unroll
+#pragma unroll 1
         for (int c0 = 0; c0 < TN; c0 += 16) {
             uint32_t r[16];
             const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
@@ -217,10 +226,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if ((q >= 8) != imag || a >= n || j >= n) continue;
                 float re = imag ? pv[q] : v[q], im = imag ? v[q] : pv[q];
                 if (EPI != 0) {
-                    const float2 lj = lam[j];
+                    const float2 lj = lam_s[c0 + q];
                     // EPI 1: divide by lam_j + conj(lam_a); EPI 2: by conj(lam_j) + lam_a
                     const float dx = lj.x + la.x, dy = EPI == 1 ? lj.y - la.y : la.y - lj.y;
-                    const float inv = 1.0f / (dx * dx + dy * dy);
+                    const float inv = __fdividef(1.0f, dx * dx + dy * dy);  // |D| >= min|D| > 0
                     const float nr = (re * dx + im * dy) * inv, ni = (im * dx - re * dy) * inv;
                     re = nr;
                     im = ni;
@@ -290,23 +299,34 @@ CUtensorMap make_map(const void *ptr, uint64_t inner, uint64_t rows, uint32_t bo
     return m;
 }
 
-template <int EPI, bool C128>
+template <int EPI, bool C128, int TN>
 void launch(const CUtensorMap &ma, const CUtensorMap &mb, int n, int np, const float2 *lam, void *out, int *status,
             cudaStream_t s) {
-    OM_CUDA_TRY(cudaFuncSetAttribute(tc_product<EPI, C128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)SMEM_BYTES));
+    constexpr size_t smem = Tile<TN>::SMEM_BYTES;
+    OM_CUDA_TRY(cudaFuncSetAttribute(tc_product<EPI, C128, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
     dim3 grid((n + TN - 1) / TN, (2 * np) / TM);
     const int kt = (2 * n + TK - 1) / TK;
-    tc_product<EPI, C128><<<grid, kThreads, SMEM_BYTES, s>>>(ma, mb, n, kt, lam, out, status, 2000000000ull);
+    tc_product<EPI, C128, TN><<<grid, kThreads, smem, s>>>(ma, mb, n, kt, lam, out, status, 2000000000ull);
     note_launch();
     OM_CHECK_LAUNCH();
+}
+
+template <int TN>
+void launch_epi(const CUtensorMap &ma, const CUtensorMap &mb, int epi, bool out_c128, int n, int np,
+                const float2 *lam, void *out, int *status, cudaStream_t s) {
+    if (out_c128) launch<0, true, TN>(ma, mb, n, np, lam, out, status, s);
+    else if (epi == 0) launch<0, false, TN>(ma, mb, n, np, lam, out, status, s);
+    else if (epi == 1) launch<1, false, TN>(ma, mb, n, np, lam, out, status, s);
+    else launch<2, false, TN>(ma, mb, n, np, lam, out, status, s);
 }
 
 }  // namespace
 
 struct NojumpTc {
     CUtensorMap opmap[8];
-    CUtensorMap tmap[3];  // t0, t1, t2
+    CUtensorMap tmap[3];  // t0, t1, t2, boxes of tn rows
+    int tn = 64;          // complex columns per tile (64 or 256)
     DBuf<int> status;
 };
 
@@ -338,8 +358,11 @@ void nojump_tc_prepare(om_nojump &M, cudaStream_t s) {
         OM_CHECK_LAUNCH();
         tc->opmap[k] = make_map(M.opx[k].p, (uint64_t)R, (uint64_t)R, TM);
     }
+    // 256-column tiles once they still give a full wave of CTAs
+    const int64_t mtiles = (2 * (int64_t)np) / TM;
+    tc->tn = mtiles * ((n + 255) / 256) >= num_sms() ? 256 : 64;
     const float2 *t[3] = {M.t0.p, M.t1.p, M.t2.p};
-    for (int k = 0; k < 3; ++k) tc->tmap[k] = make_map(t[k], 2 * (uint64_t)n, (uint64_t)n, TN);
+    for (int k = 0; k < 3; ++k) tc->tmap[k] = make_map(t[k], 2 * (uint64_t)n, (uint64_t)n, tc->tn);
 }
 
 void nojump_tc_release(om_nojump &M) {
@@ -356,12 +379,10 @@ void nojump_tc_product(const om_nojump &M, int op, int epi, const float2 *B, voi
     if (B == M.t0.p) mb = tc.tmap[0];
     else if (B == M.t1.p) mb = tc.tmap[1];
     else if (B == M.t2.p) mb = tc.tmap[2];
-    else mb = make_map(B, 2 * (uint64_t)M.n, (uint64_t)M.n, TN);
+    else mb = make_map(B, 2 * (uint64_t)M.n, (uint64_t)M.n, tc.tn);
     const CUtensorMap &ma = tc.opmap[op];
-    if (out_c128) launch<0, true>(ma, mb, M.n, M.n_pad, M.lam32.p, out, tc.status.p, s);
-    else if (epi == 0) launch<0, false>(ma, mb, M.n, M.n_pad, M.lam32.p, out, tc.status.p, s);
-    else if (epi == 1) launch<1, false>(ma, mb, M.n, M.n_pad, M.lam32.p, out, tc.status.p, s);
-    else launch<2, false>(ma, mb, M.n, M.n_pad, M.lam32.p, out, tc.status.p, s);
+    if (tc.tn == 256) launch_epi<256>(ma, mb, epi, out_c128, M.n, M.n_pad, M.lam32.p, out, tc.status.p, s);
+    else launch_epi<64>(ma, mb, epi, out_c128, M.n, M.n_pad, M.lam32.p, out, tc.status.p, s);
 }
 
 // OM_ETIMEOUT if a product gave up a wait since the last check (synchronises s)
