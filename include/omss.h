@@ -25,8 +25,9 @@
  * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *   stream).  All device work is ordered on it.  Entry points that return
  *   host-side scalars synchronise the stream before returning.
- * - Handles (om_matrix, om_ilu) own device memory allocated by the library
- *   (cudaMallocAsync on the given stream) and are released with the matching
+ * - Handles (om_matrix, om_ilu, om_nojump) own device memory allocated by the
+ *   library -- through the hook of om_set_allocator when one is set, else with
+ *   cudaMallocAsync on the given stream -- and are released with the matching
  *   *_free call.  Vectors (rho, perm, x0, gradients of rho) are caller-owned.
  * - No C++ exception crosses the ABI.  Every call returns an om_status;
  *   OM_OK is 0 and every error is negative.  om_last_error() returns a
@@ -53,7 +54,7 @@ typedef enum {
     OM_ENOCONV = -5,     /* GMRES hit max_iters; the best iterate is still written */
     OM_EBREAKDOWN = -6,  /* Arnoldi breakdown before convergence */
     OM_ENUMERIC = -7,    /* NaN or Inf met in a residual or a factor */
-    OM_ETIMEOUT = -8     /* a device-side wait exceeded wait_timeout_ns (reserved) */
+    OM_ETIMEOUT = -8     /* a device-side wait exceeded wait_timeout_ns */
 } om_status;
 
 /* Parameters of Eq. 1 and Eq. 3 (units of omega_m) and the Fock cutoffs of
@@ -81,8 +82,11 @@ typedef struct {
                                FP32, and the ILU is an approximation far coarser
                                than FP32 rounding); 1: complex128 sweeps */
     double tol;             /* target of eta = ||L x||_inf / (||L||_inf ||x||_inf) */
-    int64_t wait_timeout_ns;/* bound on device spin-waits; the current kernels
-                               synchronise with barriers only, so it is unused */
+    int64_t wait_timeout_ns;/* bound on each device-side spin-wait of the solve's
+                               kernels (mbarrier phases of the sweeps and of the
+                               tensor-core products, the split sweep's cross-block
+                               flags); a wait that runs out aborts its kernel and
+                               the solve returns OM_ETIMEOUT.  <= 0: 2 s */
 } om_solve_opts;
 
 typedef struct {
@@ -93,6 +97,29 @@ typedef struct {
     double seconds;         /* wall time of the call */
     double residual_history[64]; /* eta at the end of each cycle (first 64) */
 } om_solve_info;
+
+/* ---- device memory --------------------------------------------------------
+ * om_set_allocator routes every device allocation of the library (handles and
+ * the work space of each call) through alloc(bytes, stream, ctx) and
+ * free(ptr, stream, ctx), stream being the cudaStream_t of the call that
+ * allocates or frees (as void*).  The buffer may be used on that stream as
+ * soon as alloc returns, and free is called once the library has enqueued its
+ * last use of it on that stream (stream-ordered, as cudaFreeAsync).  Both
+ * functions must be thread-safe (the batched solve allocates from several host
+ * threads) and alloc returns NULL on failure (the call then fails with
+ * OM_ENOMEM).  A framework's caching allocator fits here, so that the factors
+ * and Krylov bases (several GB) are counted in its pool.  NULL, NULL restores
+ * cudaMallocAsync / cudaFreeAsync.  cuSOLVER's own internal work space, in the
+ * set-up of om_nojump_factor, is not routed.  Change the hook only while no
+ * handle is alive: a buffer is always freed through the hook current at that
+ * time.  No counterpart in the paper.
+ * Errors: OM_EINVAL if exactly one of alloc and free is NULL. */
+typedef void *(*om_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*om_free_fn)(void *ptr, void *stream, void *ctx);
+om_status om_set_allocator(om_alloc_fn alloc, om_free_fn free, void *ctx);
+/* Number of allocations made through the hook since the library was loaded
+ * (instrumentation). */
+int64_t om_allocator_hook_calls(void);
 
 typedef struct om_matrix om_matrix; /* complex CSR on the device */
 typedef struct om_ilu om_ilu;       /* ILU factors + sweep schedule on the device */

@@ -35,8 +35,13 @@ class om_solve_info(ctypes.Structure):
 STATUS = {0: "OM_OK", -1: "OM_EINVAL", -2: "OM_ENOMEM", -3: "OM_ECUDA", -4: "OM_EZEROPIVOT",
           -5: "OM_ENOCONV", -6: "OM_EBREAKDOWN", -7: "OM_ENUMERIC", -8: "OM_ETIMEOUT"}
 
+ALLOC_FN = ctypes.CFUNCTYPE(c_vp, ctypes.c_size_t, c_vp, c_vp)
+FREE_FN = ctypes.CFUNCTYPE(None, c_vp, c_vp, c_vp)
+
 # name -> (restype, argtypes); every entry point declared in include/omss.h
 SIGNATURES = {
+    "om_set_allocator": (c_i32, [ALLOC_FN, FREE_FN, c_vp]),
+    "om_allocator_hook_calls": (c_i64, []),
     "om_build_liouvillian": (c_i32, [ctypes.POINTER(om_params), ctypes.POINTER(om_build_opts), c_vp, ctypes.POINTER(c_vp)]),
     "om_matrix_info": (c_i32, [c_vp, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64), ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl)]),
     "om_matrix_export": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),

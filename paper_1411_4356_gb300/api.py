@@ -33,6 +33,48 @@ def _require_cuda(t: torch.Tensor, dtype, numel: int, name: str):
         raise ValueError(f"{name}: need a contiguous CUDA {dtype} tensor with {numel} elements")
 
 
+# ---------------------------------------------------------------- allocator
+_hook = None  # keeps the ctypes callbacks alive while they are installed
+
+
+def _torch_alloc(nbytes, stream, ctx):
+    try:
+        return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+    except Exception:  # noqa: BLE001 -- the library turns NULL into OM_ENOMEM
+        return None
+
+
+def _torch_free(ptr, stream, ctx):
+    torch.cuda.caching_allocator_delete(int(ptr))
+
+
+def set_allocator(alloc=None, free=None) -> None:
+    """Route the library's device allocations through alloc(nbytes, stream, ctx) -> int
+    and free(ptr, stream, ctx) (om_set_allocator); no arguments restores cudaMallocAsync."""
+    global _hook
+    lib = _lib.load()
+    if alloc is None:
+        check(lib.om_set_allocator(_lib.ALLOC_FN(), _lib.FREE_FN(), None), "om_set_allocator")
+        _hook = None
+        return
+    hook = (_lib.ALLOC_FN(alloc), _lib.FREE_FN(free))
+    check(lib.om_set_allocator(hook[0], hook[1], None), "om_set_allocator")
+    _hook = hook
+
+
+def use_torch_allocator(on: bool = True) -> None:
+    """Take the library's device memory from PyTorch's caching allocator (so that
+    factors and Krylov bases are counted in torch.cuda.memory_allocated)."""
+    if on:
+        set_allocator(_torch_alloc, _torch_free)
+    else:
+        set_allocator()
+
+
+def allocator_hook_calls() -> int:
+    return int(_lib.load().om_allocator_hook_calls())
+
+
 def to_om_params(p: SystemParams) -> om_params:
     return om_params(p.Nc, p.Nm, p.omega_m, p.Delta, p.kappa, p.g0, p.E, p.Q_m, p.n_th)
 
@@ -255,7 +297,8 @@ def nojump_apply(M: NoJump, v: torch.Tensor, adjoint: bool = False, stream=None)
 
 def steady_state_solve_nojump(A: Matrix, M: NoJump, restart: int = 50, max_iters: int = 5000, tol: float = 1e-10,
                               precision: int = 0, x0: torch.Tensor | None = None, stream=None,
-                              raise_on_noconv: bool = True, rho_out: torch.Tensor | None = None):
+                              raise_on_noconv: bool = True, rho_out: torch.Tensor | None = None,
+                              wait_timeout_ns: int = 0):
     """Sec. IV's GMRES on the unpermuted L~ with the no-jump preconditioner:
     rho (n x n complex128 CUDA tensor) and SolveInfo."""
     lib = _lib.load()
@@ -264,7 +307,7 @@ def steady_state_solve_nojump(A: Matrix, M: NoJump, restart: int = 50, max_iters
     _require_cuda(flat, torch.complex128, n * n, "rho_out")
     if x0 is not None:
         _require_cuda(x0, torch.complex128, A.N, "x0")
-    o = _opts(restart, max_iters, tol, precision, 0)
+    o = _opts(restart, max_iters, tol, precision, wait_timeout_ns)
     info = om_solve_info()
     st = lib.om_steady_state_solve_nojump(A.handle, M.handle, ctypes.byref(o), _ptr(x0), _ptr(flat),
                                           ctypes.byref(info), ctypes.c_void_p(_stream(stream)))

@@ -19,6 +19,47 @@ struct ProfState {
 ProfState g_prof;
 }  // namespace
 void set_error(const std::string &msg) { g_last_error = msg; }
+
+WaitContext &wait_context() {
+    thread_local WaitContext ctx;
+    return ctx;
+}
+
+namespace {
+struct AllocHook {
+    om_alloc_fn alloc = nullptr;
+    om_free_fn free = nullptr;
+    void *ctx = nullptr;
+};
+std::mutex g_alloc_mu;
+AllocHook g_alloc;
+std::atomic<int64_t> g_hook_allocs{0};
+
+AllocHook current_hook() {
+    std::lock_guard<std::mutex> g(g_alloc_mu);
+    return g_alloc;
+}
+}  // namespace
+
+void *dev_alloc(size_t bytes, cudaStream_t s) {
+    const AllocHook h = current_hook();
+    void *p = nullptr;
+    if (h.alloc) {
+        p = h.alloc(bytes, reinterpret_cast<void *>(s), h.ctx);
+        if (!p) throw Error{OM_ENOMEM, "the allocator set by om_set_allocator returned NULL for " +
+                                           std::to_string(bytes) + " bytes"};
+        g_hook_allocs.fetch_add(1, std::memory_order_relaxed);
+        return p;
+    }
+    OM_CUDA_TRY(cudaMallocAsync(&p, bytes, s));
+    return p;
+}
+
+void dev_free(void *p, cudaStream_t s) {
+    const AllocHook h = current_hook();
+    if (h.free) h.free(p, reinterpret_cast<void *>(s), h.ctx);
+    else cudaFreeAsync(p, s);
+}
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 ProfScope::ProfScope(int cat_, cudaStream_t s_) : cat(cat_), s(s_), on(g_prof.on.load()) {
@@ -134,3 +175,15 @@ void csr_to_host(const om_matrix &A, std::vector<int64_t> &rp, std::vector<int32
     OM_CUDA_TRY(cudaStreamSynchronize(s));
 }
 }  // namespace omss
+
+extern "C" om_status om_set_allocator(om_alloc_fn alloc, om_free_fn free, void *ctx) {
+    return guarded([&] {
+        OM_REQUIRE((alloc == nullptr) == (free == nullptr), "om_set_allocator: give both functions or neither");
+        std::lock_guard<std::mutex> g(g_alloc_mu);
+        g_alloc.alloc = alloc;
+        g_alloc.free = free;
+        g_alloc.ctx = alloc ? ctx : nullptr;
+    });
+}
+
+extern "C" int64_t om_allocator_hook_calls(void) { return g_hook_allocs.load(); }

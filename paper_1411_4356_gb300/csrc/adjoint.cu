@@ -166,6 +166,7 @@ void ensure_conj_transpose(const om_matrix &A, cudaStream_t s) {
 using namespace omss;
 
 namespace omss {
+bool wait_gave_up(const int *status, cudaStream_t s);
 namespace {
 // GMRES on A^H mu = G (G permuted into the solver's order by perm, NULL =
 // natural order) and the contraction dF/dtheta = -Re(mu^H dA/dtheta rho).
@@ -175,10 +176,14 @@ om_status adjoint_solve(const om_matrix *A, const int32_t *perm_dev, const om_so
                         const double *rho_dev, const double *grad_rho_dev, double grad_out[4], om_solve_info *info,
                         void *stream, MakeOps make_ops) {
     om_status final_status = OM_OK;
+    DBuf<int> wstatus;
+    cudaStream_t s = as_stream(stream);
     om_status st = guarded([&] {
         auto t0 = std::chrono::steady_clock::now();
-        cudaStream_t s = as_stream(stream);
         const int64_t N = A->N;
+        wstatus.alloc(1, s);
+        OM_CUDA_TRY(cudaMemsetAsync(wstatus.p, 0, sizeof(int), s));
+        WaitScope waits((uint64_t)std::max<int64_t>(opts->wait_timeout_ns, 0), wstatus.p);
         ensure_conj_transpose(*A, s);
         GmresWork<double2> W;
         W.alloc(N, opts->restart, s);
@@ -208,6 +213,11 @@ om_status adjoint_solve(const om_matrix *A, const int32_t *perm_dev, const om_so
                 ++cycles;
                 rel = r.beta / gnorm;  // true residual at the start of this cycle
                 if (cycles <= 64) inf.residual_history[cycles - 1] = r.last_estimate / gnorm;
+                if (wait_gave_up(wstatus.p, s)) {
+                    final_status = OM_ETIMEOUT;
+                    set_error("om_steady_state_adjoint: a device-side wait exceeded wait_timeout_ns");
+                    break;
+                }
                 if (r.breakdown) {
                     final_status = OM_EBREAKDOWN;
                 set_error("om_steady_state_adjoint: GMRES breakdown");
@@ -251,6 +261,7 @@ om_status adjoint_solve(const om_matrix *A, const int32_t *perm_dev, const om_so
         part.release(s);
         sums.release(s);
     });
+    wstatus.release(s);
     return st != OM_OK ? st : final_status;
 }
 }  // namespace

@@ -78,13 +78,16 @@ __device__ inline double2 bwarp_sum(double2 v) {
 }
 
 // ---- preconditioner: z_j = U^{-1} L^{-1} v_j, one block per system
-__global__ void __launch_bounds__(kPrecondThreads, 1) b_precond(const BSys *sys, const int *active, int j) {
+__global__ void __launch_bounds__(kPrecondThreads, 1) b_precond(const BSys *sys, const int *active, int j,
+                                                                 unsigned long long limit_ns, int *status) {
     const int s = blockIdx.x;
     if (!active[s]) return;
     const BSys &S = sys[s];
     extern __shared__ __align__(128) unsigned char smem_raw[];
     tsw::SweepSmem<float2, kWin, kStages> sm;
     sm.carve(smem_raw);
+    sm.limit_ns = limit_ns;
+    sm.status = status;
     sm.init();
     const double2 *v = S.V + (int64_t)j * S.N;
     for (int64_t i = threadIdx.x; i < S.N; i += blockDim.x) S.tmp[i] = make_float2((float)v[i].x, (float)v[i].y);
@@ -552,7 +555,9 @@ void solve_lockstep(int32_t count, const om_matrix *const *A_rcm, const om_ilu *
                 upload_active(running);
                 {
                     ProfScope prof(PROF_SWEEP, s);
-                    b_precond<<<(unsigned)count, kPrecondThreads, psmem, s>>>(dsys.p, dactive.p, j);
+                    b_precond<<<(unsigned)count, kPrecondThreads, psmem, s>>>(dsys.p, dactive.p, j,
+                                                                              wait_context().limit_ns,
+                                                                              wait_context().status);
                     omss::note_launch();
                 }
                 {

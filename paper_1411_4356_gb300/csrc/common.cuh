@@ -73,6 +73,35 @@ om_status guarded(F &&body) {
 }
 
 // ------------------------------------------------------- device buffers
+// Every device allocation of the library goes through these two calls: the
+// hook set by om_set_allocator if any, else cudaMallocAsync / cudaFreeAsync
+// on the given stream (abi.cu).  dev_alloc throws OM_ENOMEM on failure.
+void *dev_alloc(size_t bytes, cudaStream_t s);
+void dev_free(void *p, cudaStream_t s);
+
+// ------------------------------------------------------- device-side waits
+// Every spin-wait of the library's kernels (mbarrier phases, shared counters,
+// cross-block flags) gives up after a time limit; a wait that gives up aborts
+// its kernel, which then drains its own copies in flight (bounded by
+// kDrainNs), frees its tensor memory and sets *status to 1.  The limit and the
+// status word come from the calling host thread's WaitContext, which the solves
+// set from om_solve_opts.wait_timeout_ns (<= 0: kDefaultWaitNs).
+constexpr uint64_t kDefaultWaitNs = 2000000000ull;
+constexpr uint64_t kDrainNs = 2000000000ull;
+struct WaitContext {
+    uint64_t limit_ns = kDefaultWaitNs;
+    int *status = nullptr;  // device int, or NULL
+};
+WaitContext &wait_context();  // per host thread
+struct WaitScope {
+    WaitContext saved;
+    WaitScope(uint64_t limit_ns, int *status) : saved(wait_context()) {
+        wait_context().limit_ns = limit_ns > 0 ? limit_ns : kDefaultWaitNs;
+        wait_context().status = status;
+    }
+    ~WaitScope() { wait_context() = saved; }
+};
+
 // Stream-ordered device allocation owned by a handle.
 template <class T>
 struct DBuf {
@@ -81,10 +110,10 @@ struct DBuf {
     void alloc(size_t count, cudaStream_t s) {
         release(s);
         n = count;
-        if (count) OM_CUDA_TRY(cudaMallocAsync((void **)&p, sizeof(T) * count, s));
+        if (count) p = static_cast<T *>(dev_alloc(sizeof(T) * count, s));
     }
     void release(cudaStream_t s) {
-        if (p) cudaFreeAsync(p, s);
+        if (p) dev_free(p, s);
         p = nullptr;
         n = 0;
     }

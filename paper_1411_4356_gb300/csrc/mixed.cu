@@ -83,15 +83,21 @@ void ensure_values_c64(const om_matrix &A, cudaStream_t s) {
     OM_CHECK_LAUNCH();
 }
 
+bool wait_gave_up(const int *status, cudaStream_t s);
+
 namespace {
 // the refinement loop around an inner complex64 operator/preconditioner pair
 om_status mixed_solve(const om_matrix *A, KrylovOps<float2> &ops, const int32_t *perm_dev, const om_solve_opts *opts,
                       const double *x0, double *rho_dev, om_solve_info *info, void *stream, bool csr_c64) {
     om_status final_status = OM_OK;
+    DBuf<int> wstatus;
+    cudaStream_t s = as_stream(stream);
     om_status st = guarded([&] {
         auto t0 = std::chrono::steady_clock::now();
-        cudaStream_t s = as_stream(stream);
         const int64_t N = A->N;
+        wstatus.alloc(1, s);
+        OM_CUDA_TRY(cudaMemsetAsync(wstatus.p, 0, sizeof(int), s));
+        WaitScope waits((uint64_t)std::max<int64_t>(opts->wait_timeout_ns, 0), wstatus.p);
         if (csr_c64) ensure_values_c64(*A, s);
         GmresWork<double2> W64;
         W64.alloc(N, 1, s);
@@ -122,6 +128,11 @@ om_status mixed_solve(const om_matrix *A, KrylovOps<float2> &ops, const int32_t 
             if (steps > 0) {
                 eta = eta_of(*A, x.p, W64.w.p, W64, s);
                 if (steps <= 64) inf.residual_history[steps - 1] = eta;
+                if (wait_gave_up(wstatus.p, s)) {
+                    final_status = OM_ETIMEOUT;
+                    set_error("om_steady_state_solve (mixed precision): a device-side wait exceeded wait_timeout_ns");
+                    break;
+                }
                 if (!std::isfinite(eta)) {
                     final_status = OM_ENUMERIC;
                 set_error("om_steady_state_solve (mixed precision): non-finite residual (unstable preconditioner?)");
@@ -153,6 +164,11 @@ om_status mixed_solve(const om_matrix *A, KrylovOps<float2> &ops, const int32_t 
             omss::note_launch();
             OM_CHECK_LAUNCH();
             ++steps;
+            if (broke && wait_gave_up(wstatus.p, s)) {
+                final_status = OM_ETIMEOUT;
+                set_error("om_steady_state_solve (mixed precision): a device-side wait exceeded wait_timeout_ns");
+                break;
+            }
             if (broke) {
                 final_status = OM_EBREAKDOWN;
                 set_error("om_steady_state_solve (mixed precision): GMRES breakdown");
@@ -175,6 +191,7 @@ om_status mixed_solve(const om_matrix *A, KrylovOps<float2> &ops, const int32_t 
         r32.release(s);
         d32.release(s);
     });
+    wstatus.release(s);
     return st != OM_OK ? st : final_status;
 }
 }  // namespace

@@ -21,10 +21,11 @@
 //                   apply the elementwise division by D where asked and store
 //                   complex64 (rounded to TF32 for the next product) or
 //                   complex128.
-// Every mbarrier wait is bounded (time limit on %globaltimer); a wait that
-// gives up sets an abort flag, the block drains its copies in flight, frees
-// its tensor memory and records OM_ETIMEOUT in a device status word that the
-// host reads at the end of the apply or solve.
+// Every mbarrier wait is bounded (the calling thread's wait limit, on
+// %globaltimer); a wait that gives up sets an abort flag, the block drains its
+// copies and products in flight (bounded by kDrainNs), frees its tensor memory
+// and sets a device status word (the solve's, else the handle's) that the host
+// reads at the end of the apply or solve and reports as OM_ETIMEOUT.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (*abort_flag)  // let the copies already issued land before the block leaves
             for (int kt = issued > STAGES ? issued - STAGES : 0; kt < issued; ++kt)
-                mb_drain(&full[kt % STAGES], (kt / STAGES) & 1, limit_ns);
+                mb_drain(&full[kt % STAGES], (kt / STAGES) & 1, kDrainNs);
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
         for (int kt = 0; kt < kt_count; ++kt) {
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncwarp();
     // epilogue (all warps): wait for the accumulator, bounded even on abort
-    mb_drain(done, 0, limit_ns);
+    mb_drain(done, 0, kDrainNs);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const bool ok = __all_sync(0xffffffffu, mb_try(done, 0) && !*abort_flag);
     if (ok) {
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)TN) : "memory");
     }
-    if (threadIdx.x == 0 && !ok) atomicExch(status, (int)OM_ETIMEOUT);
+    if (threadIdx.x == 0 && !ok) atomicExch(status, 1);
 }
 
 // op[k] (row-major complex64 n x n) -> the expanded real matrix, 2 np x 2 np, rounded to TF32
@@ -307,7 +308,9 @@ void launch(const CUtensorMap &ma, const CUtensorMap &mb, int n, int np, const f
                                      (int)smem));
     dim3 grid((n + TN - 1) / TN, (2 * np) / TM);
     const int kt = (2 * n + TK - 1) / TK;
-    tc_product<EPI, C128, TN><<<grid, kThreads, smem, s>>>(ma, mb, n, kt, lam, out, status, 2000000000ull);
+    const WaitContext &wc = wait_context();
+    tc_product<EPI, C128, TN><<<grid, kThreads, smem, s>>>(ma, mb, n, kt, lam, out, wc.status ? wc.status : status,
+                                                            wc.limit_ns);
     note_launch();
     OM_CHECK_LAUNCH();
 }

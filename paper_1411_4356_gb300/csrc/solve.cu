@@ -180,13 +180,24 @@ om_status solve_mixed(const om_matrix *A, const om_ilu *M, const int32_t *perm_d
 namespace omss {
 // The FP64 restarted GMRES of Sec. IV around a given operator/preconditioner
 // pair; perm (NULL: natural order) scatters the normalised x into rho.
+bool wait_gave_up(const int *status, cudaStream_t s) {
+    int h = 0;
+    OM_CUDA_TRY(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    OM_CUDA_TRY(cudaStreamSynchronize(s));
+    return h != 0;
+}
+
 om_status fp64_solve(const om_matrix *A, KrylovOps<double2> &ops, GmresWork<double2> &W, const int32_t *perm_dev,
                      const om_solve_opts *opts, const double *x0, double *rho_dev, om_solve_info *info,
                      cudaStream_t s) {
     om_status final_status = OM_OK;
+    DBuf<int> wstatus;
     om_status st = guarded([&] {
         auto t0 = std::chrono::steady_clock::now();
         const int64_t N = A->N;
+        wstatus.alloc(1, s);
+        OM_CUDA_TRY(cudaMemsetAsync(wstatus.p, 0, sizeof(int), s));
+        WaitScope waits((uint64_t)std::max<int64_t>(opts->wait_timeout_ns, 0), wstatus.p);
         DBuf<double2> b, x;
         b.alloc(N, s);
         x.alloc(N, s);
@@ -207,6 +218,11 @@ om_status fp64_solve(const om_matrix *A, KrylovOps<double2> &ops, GmresWork<doub
             eta = eta_of(*A, x.p, W.w.p, W, s);
             dev_stats<double2>(x.p, N, W, s, nullptr, &xinf);
             if (cycles <= 64) inf.residual_history[cycles - 1] = eta;
+            if (wait_gave_up(wstatus.p, s)) {
+                final_status = OM_ETIMEOUT;
+                set_error("om_steady_state_solve: a device-side wait exceeded wait_timeout_ns");
+                break;
+            }
             if (!std::isfinite(eta)) {
                 final_status = OM_ENUMERIC;
                 set_error("om_steady_state_solve: non-finite residual (unstable preconditioner?)");
@@ -239,6 +255,7 @@ om_status fp64_solve(const om_matrix *A, KrylovOps<double2> &ops, GmresWork<doub
         b.release(s);
         x.release(s);
     });
+    wstatus.release(s);
     return st != OM_OK ? st : final_status;
 }
 

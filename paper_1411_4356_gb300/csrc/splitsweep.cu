@@ -62,7 +62,6 @@ constexpr int kSplitThreads = kSplitWarps * 32;
 constexpr int kHelperWarps = 8;                 // warps per helper block that take units
 constexpr int kWinRows = 2048;                  // shared window of recent x values
 constexpr int kStages = 8, kGStages = 4, kFarRing = 32;
-constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr unsigned long long kEmpty = ~0ull;    // "not written yet" in xs and the partials
 static_assert(kSweepLag >= 2 && kSweepLag < kWinRows / kTile - 2, "near band must fit the window");
 static_assert(kUnitSlots <= 32, "unit slots");
@@ -85,6 +84,8 @@ struct SplitArgs {
     unsigned long long *xs;        // N, x in sweep order; kEmpty at launch
     unsigned long long *far_part;  // nunits x 32; kEmpty at launch
     int *ctrl;                     // [0] finished tiles (hint), [32] global abort; zero at launch
+    unsigned long long limit_ns;   // bound on each wait
+    int *status;                   // device word set to 1 when a wait gave up (may be NULL)
 };
 
 struct SplitSmem {
@@ -157,14 +158,14 @@ __device__ inline float2 unpack(unsigned long long u) {
 }
 
 // Waits until a shared counter reaches `target`; false once the block aborts
-// or after kWaitNs (which aborts it).
-__device__ inline bool wait_shared_ge(volatile int *flag, int target, volatile int *abort) {
+// or after limit_ns (which aborts it).
+__device__ inline bool wait_shared_ge(volatile int *flag, int target, volatile int *abort, uint64_t limit_ns) {
     if (ld_acquire_cta(flag) >= target) return true;
     const uint64_t start = now_ns();
     for (;;) {
         if (*abort) return false;
         if (ld_acquire_cta(flag) >= target) return true;
-        if (now_ns() - start > kWaitNs) {
+        if (now_ns() - start > limit_ns) {
             *abort = 1;
             return false;
         }
@@ -173,16 +174,16 @@ __device__ inline bool wait_shared_ge(volatile int *flag, int target, volatile i
 
 // A bounded retry loop for the cross-block waits: `ready()` is polled with a
 // pause of `pause_ns` in between; false on a global or block abort or after
-// kWaitNs (which sets the global abort).
+// limit_ns (which sets the global abort).
 template <class F>
-__device__ inline bool poll_until(F &&ready, int *gabort, volatile int *abort, unsigned pause_ns) {
+__device__ inline bool poll_until(F &&ready, int *gabort, volatile int *abort, unsigned pause_ns, uint64_t limit_ns) {
     if (ready()) return true;
     const uint64_t start = now_ns();
     for (;;) {
         if (ld_relaxed_gpu(gabort) || (abort && *abort)) return false;
         __nanosleep(pause_ns);
         if (ready()) return true;
-        if (now_ns() - start > kWaitNs) {
+        if (now_ns() - start > limit_ns) {
             atomicExch(gabort, 1);
             if (abort) *abort = 1;
             return false;
@@ -229,7 +230,7 @@ __device__ void main_block(const SplitArgs &a) {
         bool stop = false;
         for (int64_t T = 0; T < ntiles && !*abort && !stop; ++T) {
             const int gs = (int)(T % kGStages);
-            if (T >= kGStages && !wait_phase(&sm.gempty[gs], (uint32_t)((T / kGStages - 1) & 1), abort)) break;
+            if (T >= kGStages && !wait_phase(&sm.gempty[gs], (uint32_t)((T / kGStages - 1) & 1), abort, a.limit_ns)) break;
             constexpr uint32_t kMat = kTile * kTile * sizeof(float2);
             mbar_expect_tx(&sm.gfull[gs], 2 * kMat);
             bulk_g2s(sm.ghring + gs * 2 * kTile * kTile, a.G + T * kTile * kTile, kMat, &sm.gfull[gs]);
@@ -241,7 +242,7 @@ __device__ void main_block(const SplitArgs &a) {
                 const int ns = min(kChunkSlots, wn - c);
                 const int stage = (int)(g % kStages);
                 const uint32_t use = (uint32_t)(g / kStages);
-                if (g >= kStages && !wait_phase(&sm.empty[stage], (use - 1) & 1, abort)) {
+                if (g >= kStages && !wait_phase(&sm.empty[stage], (use - 1) & 1, abort, a.limit_ns)) {
                     stop = true;
                     break;
                 }
@@ -263,7 +264,7 @@ __device__ void main_block(const SplitArgs &a) {
     if (warp == kPublisherWarp) {
         int done = 0;
         while (done < ntiles) {
-            if (!wait_shared_ge(sm.xdone, done + 1, abort)) break;
+            if (!wait_shared_ge(sm.xdone, done + 1, abort, a.limit_ns)) break;
             const int xd = ld_acquire_cta(sm.xdone);
             for (int T = done; T < xd; ++T) {
                 const int64_t t = (int64_t)T * kTile + lane;
@@ -282,7 +283,10 @@ __device__ void main_block(const SplitArgs &a) {
             done = xd;
         }
         if (done < ntiles) {  // aborted: the rows not written read as NaN
-            if (lane == 0) atomicExch(gabort, 1);
+            if (lane == 0) {
+                atomicExch(gabort, 1);
+                if (a.status) atomicExch(a.status, 1);
+            }
             const float nan = __int_as_float(0x7fc00000);
             for (int64_t t = (int64_t)done * kTile + lane; t < N; t += 32)
                 a.z[rowof(t, N, a.forward)] = make_float2(nan, nan);
@@ -317,7 +321,7 @@ __device__ void main_block(const SplitArgs &a) {
                     }
                     return __all_sync(0xffffffffu, ok);
                 };
-                if (!poll_until(there, gabort, abort, 32)) {
+                if (!poll_until(there, gabort, abort, 32, a.limit_ns)) {
                     *abort = 1;
                     break;
                 }
@@ -335,7 +339,7 @@ __device__ void main_block(const SplitArgs &a) {
             asm volatile("bar.sync %0, %1;" ::"r"(2 + team), "n"(kTeam * 32) : "memory");
             if (member == 0) {
                 // farsum[slot] is free once the finisher has read tile T - kFarRing
-                if (T >= kFarRing) wait_shared_ge(sm.findone, (int)(T - kFarRing + 1), abort);
+                if (T >= kFarRing) wait_shared_ge(sm.findone, (int)(T - kFarRing + 1), abort, a.limit_ns);
                 float2 f = gp[lane];
 #pragma unroll
                 for (int k = 1; k < kTeam; ++k) f = O::add(f, gp[k * kTile + lane]);
@@ -353,9 +357,9 @@ __device__ void main_block(const SplitArgs &a) {
             const int64_t t = T * kTile + lane;
             const int slot = (int)(T % kFarRing);
             const int gs = (int)(T % kGStages);
-            const bool fr = wait_shared_ge(&sm.farflag[slot], (int)(T + 1), abort);
-            wait_phase(&sm.gfull[gs], (uint32_t)((T / kGStages) & 1), abort);
-            wait_phase(&sm.pfull[T & 1], (uint32_t)((T >> 1) & 1), abort);
+            const bool fr = wait_shared_ge(&sm.farflag[slot], (int)(T + 1), abort, a.limit_ns);
+            wait_phase(&sm.gfull[gs], (uint32_t)((T / kGStages) & 1), abort, a.limit_ns);
+            wait_phase(&sm.pfull[T & 1], (uint32_t)((T >> 1) & 1), abort, a.limit_ns);
             float2 y = O::zero();
             if (fr && t < N) {
                 float2 s4[4] = {O::zero(), O::zero(), O::zero(), O::zero()};
@@ -373,7 +377,7 @@ __device__ void main_block(const SplitArgs &a) {
 #pragma unroll
             for (int c = 0; c < kTile; ++c) x4[c & 3] = O::fma(G[c * kTile + lane], sm.ybuf[c], x4[c & 3]);
             // cbuf[T % 2] is free once the solver has used c_{T-2}
-            if (T >= 2) wait_shared_ge(sm.maindone, (int)(T - 1), abort);
+            if (T >= 2) wait_shared_ge(sm.maindone, (int)(T - 1), abort, a.limit_ns);
             sm.cbuf[(T & 1) * kTile + lane] = O::add(O::add(x4[0], x4[1]), O::add(x4[2], x4[3]));
             __syncwarp();
             if (lane == 0) {
@@ -390,14 +394,14 @@ __device__ void main_block(const SplitArgs &a) {
         int64_t g = 0;
         for (int64_t T = 0; T < ntiles; ++T) {
             // x up to tile T-2 is in the window and part[T % 2] is free again
-            wait_shared_ge(sm.xdone, (int)(T - 1), abort);
+            wait_shared_ge(sm.xdone, (int)(T - 1), abort, a.limit_ns);
             const int wn = a.near_w[T];
             float2 acc0 = O::zero(), acc1 = O::zero(), acc2 = O::zero();
             bool ok = true;
             for (int c = 0; c < wn; c += kChunkSlots, ++g) {
                 const int ns = min(kChunkSlots, wn - c);
                 const int stage = (int)(g % kStages);
-                if (!wait_phase(&sm.full[stage], (uint32_t)((g / kStages) & 1), abort)) ok = false;
+                if (!wait_phase(&sm.full[stage], (uint32_t)((g / kStages) & 1), abort, a.limit_ns)) ok = false;
                 if (ok) {
                     const int32_t *cs = sm.col_s + stage * kChunkSlots * kTile;
                     const float2 *vs = sm.val_s + stage * kChunkSlots * kTile;
@@ -428,8 +432,8 @@ __device__ void main_block(const SplitArgs &a) {
         const int64_t t = T * kTile + lane;
         const int gs = (int)(T % kGStages);
         sm.ybuf[kTile + lane] = xprev;
-        wait_phase(&sm.gfull[gs], (uint32_t)((T / kGStages) & 1), abort);
-        wait_shared_ge(sm.cflag, (int)(T + 1), abort);
+        wait_phase(&sm.gfull[gs], (uint32_t)((T / kGStages) & 1), abort, a.limit_ns);
+        wait_shared_ge(sm.cflag, (int)(T + 1), abort, a.limit_ns);
         __syncwarp();
         const float2 *Hm = sm.ghring + gs * 2 * kTile * kTile + kTile * kTile;
         float2 h4[4] = {O::zero(), O::zero(), O::zero(), O::zero()};
@@ -443,7 +447,7 @@ __device__ void main_block(const SplitArgs &a) {
         }
         // tile T reuses the window rows of tile T - kWinRows/32: published by now?
         const int64_t need_pub = T + 1 - (kWinRows / kTile - 1);
-        if (need_pub > 0) wait_shared_ge(sm.pubdone, (int)need_pub, abort);
+        if (need_pub > 0) wait_shared_ge(sm.pubdone, (int)need_pub, abort, a.limit_ns);
         if (*abort) x.x = x.y = __int_as_float(0x7fc00000);
         if (t >= N) x = O::zero();
         sm.win[t & (kWinRows - 1)] = x;
@@ -479,7 +483,7 @@ __device__ void helper_block(const SplitArgs &a) {
         const int need = U.tile - a.lag - 2;
         if (seen < need) {
             const unsigned pause = (unsigned)min((need - seen) * 128, 8192);
-            if (!poll_until([&] { return (seen = ld_relaxed_gpu(a.ctrl)) >= need; }, gabort, nullptr, pause)) return;
+            if (!poll_until([&] { return (seen = ld_relaxed_gpu(a.ctrl)) >= need; }, gabort, nullptr, pause, a.limit_ns)) return;
         }
         unsigned long long xw[kUnitSlots];
 #pragma unroll
@@ -493,7 +497,7 @@ __device__ void helper_block(const SplitArgs &a) {
             }
             return __all_sync(0xffffffffu, ok);
         };
-        if (!poll_until(all_there, gabort, nullptr, 64)) return;
+        if (!poll_until(all_there, gabort, nullptr, 64, a.limit_ns)) return;
         float2 acc = make_float2(0, 0);
 #pragma unroll
         for (int q = 0; q < kUnitSlots; ++q) acc = TOps<float2>::fma(val[q], unpack(xw[q]), acc);
@@ -554,6 +558,8 @@ bool split_sweep_c64(const TilePlan &P, const float2 *v, float2 *z, cudaStream_t
     a.xs = xs.p;
     a.far_part = part.p;
     a.ctrl = ctrl.p;
+    a.limit_ns = wait_context().limit_ns;
+    a.status = wait_context().status;
     void *args[] = {&a};
     {
         ProfScope prof(PROF_SPLIT, s);

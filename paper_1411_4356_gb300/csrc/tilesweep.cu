@@ -52,10 +52,12 @@ template <class CT, int WIN, int STAGES>
 __global__ void __launch_bounds__((kTileWarps + 1) * 32, 1)
 tile_sweep(int64_t N, int64_t ntiles, int forward, const int64_t *__restrict__ tile_ptr,
            const int32_t *__restrict__ scol, const CT *__restrict__ sval, const CT *__restrict__ G,
-           const CT *v, CT *z) {
+           const CT *v, CT *z, unsigned long long limit_ns, int *status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     tsw::SweepSmem<CT, WIN, STAGES> sm;
     sm.carve(smem_raw);
+    sm.limit_ns = limit_ns;
+    sm.status = status;
     sm.init();
     __syncthreads();
     tsw::sweep_block<CT, WIN, STAGES>(sm, N, ntiles, forward, tile_ptr, scol, sval, G, v, z, 0);
@@ -277,7 +279,9 @@ static void launch_tile(const TilePlan &P, const CT *val, const CT *G, const CT 
     auto k = tile_sweep<CT, WIN, STAGES>;
     OM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ProfScope prof(PROF_SWEEP, s);
-    k<<<1, (kTileWarps + 1) * 32, smem, s>>>(P.N, P.ntiles, P.forward ? 1 : 0, P.tile_ptr.p, P.col.p, val, G, v, z);
+    const WaitContext &wc = wait_context();
+    k<<<1, (kTileWarps + 1) * 32, smem, s>>>(P.N, P.ntiles, P.forward ? 1 : 0, P.tile_ptr.p, P.col.p, val, G, v, z,
+                                             wc.limit_ns, wc.status);
     omss::note_launch();
     OM_CHECK_LAUNCH();
 }

@@ -63,15 +63,15 @@ __device__ inline uint64_t now_ns() {
 }
 __device__ inline void consumer_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(kTileWarps * 32) : "memory"); }
 
-// Waits for an mbarrier phase; gives up after 2 s or once `abort` is set,
-// setting `abort` so that every other wait of the block returns at once.
-__device__ inline bool wait_phase(uint64_t *bar, uint32_t parity, volatile int *abort) {
+// Waits for an mbarrier phase; gives up after limit_ns or once `abort` is
+// set, setting `abort` so that every other wait of the block returns at once.
+__device__ inline bool wait_phase(uint64_t *bar, uint32_t parity, volatile int *abort, uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t start = now_ns();
     for (;;) {
         if (*abort) return false;
         if (mbar_try_wait(bar, parity)) return true;
-        if (now_ns() - start > 2000000000ull) {
+        if (now_ns() - start > limit_ns) {
             *abort = 1;
             return false;
         }
@@ -102,6 +102,8 @@ struct SweepSmem {
     CT *val_s, *win, *part, *gs;
     uint64_t *full, *empty;
     volatile int *abort_flag;
+    uint64_t limit_ns = 2000000000ull;  // bound on each wait (set by the kernel from its caller)
+    int *status = nullptr;              // device word set to 1 when a wait gave up
     static constexpr size_t bytes() {
         return sizeof(int32_t) * STAGES * kChunkSlots * kTile + sizeof(CT) * STAGES * kChunkSlots * kTile +
                sizeof(CT) * (WIN + kTileWarps * kTile + kTile * kTile) + 2 * STAGES * sizeof(uint64_t) + 16;
@@ -154,7 +156,7 @@ __device__ void sweep_block(SweepSmem<CT, WIN, STAGES> &sm, int64_t N, int64_t n
                     const int ns = (int)((width - c) < kChunkSlots ? (width - c) : kChunkSlots);
                     const int stage = (int)(g % STAGES);
                     const uint32_t use = (uint32_t)(g / STAGES);
-                    if (g >= STAGES && !wait_phase(&empty[stage], (use - 1) & 1, sm.abort_flag)) {
+                    if (g >= STAGES && !wait_phase(&empty[stage], (use - 1) & 1, sm.abort_flag, sm.limit_ns)) {
                         stop = true;
                         break;
                     }
@@ -192,7 +194,7 @@ __device__ void sweep_block(SweepSmem<CT, WIN, STAGES> &sm, int64_t N, int64_t n
         for (int64_t c = 0; c < width; c += kChunkSlots, ++g) {
             const int ns = (int)((width - c) < kChunkSlots ? (width - c) : kChunkSlots);
             const int stage = (int)(g % STAGES);
-            if (!wait_phase(&full[stage], (uint32_t)((g / STAGES) & 1), sm.abort_flag)) ok = false;
+            if (!wait_phase(&full[stage], (uint32_t)((g / STAGES) & 1), sm.abort_flag, sm.limit_ns)) ok = false;
             if (ok) {
                 const int32_t *cs = col_s + stage * kChunkSlots * kTile;
                 const CT *vs = val_s + stage * kChunkSlots * kTile;
@@ -235,6 +237,7 @@ __device__ void sweep_block(SweepSmem<CT, WIN, STAGES> &sm, int64_t N, int64_t n
         }
         consumer_barrier();
     }
+    if (threadIdx.x == 0 && abort_flag && sm.status) atomicExch(sm.status, 1);
 }
 
 

@@ -42,3 +42,11 @@ def test_oracle_is_not_linked_into_the_library():
     """The product library shares no code with the oracle."""
     out = os.popen(f"nm -D {build.LIB}").read()
     assert "oracle_" not in out
+
+
+def test_set_allocator_argument_checks_without_gpu():
+    lib = _lib.load()
+    assert lib.om_set_allocator(_lib.ALLOC_FN(), _lib.FREE_FN(), None) == 0
+    only_alloc = _lib.ALLOC_FN(lambda n, s, c: None)
+    assert lib.om_set_allocator(only_alloc, _lib.FREE_FN(), None) == -1
+    assert lib.om_allocator_hook_calls() >= 0
