@@ -111,6 +111,25 @@ def observables(p: Params, rho: np.ndarray) -> dict:
     return {"n_a": expect(na, rho).real, "n_b": expect(nb, rho).real}
 
 
+def phonon_distribution(p: Params, rho: np.ndarray) -> np.ndarray:
+    """P(m) = <m| Tr_cavity(rho) |m>, the phonon number distribution of Fig. 5:
+    the reduced mechanical state Tr_a(rho) written out with the tensor order of
+    Sec. III (h = c N_m + m) by summing the cavity blocks."""
+    n = p.Nc * p.Nm
+    r = np.asarray(rho).reshape(p.Nc, p.Nm, p.Nc, p.Nm)
+    rho_m = np.einsum("cmcl->ml", r)  # partial trace over the cavity
+    assert rho_m.shape == (p.Nm, p.Nm) and n == p.Nc * p.Nm
+    return np.real(np.diag(rho_m))
+
+
+def fano_factor(P: np.ndarray) -> float:
+    """F = <(Delta N_b)^2> / <N_b> of a phonon distribution (Sec. V)."""
+    m = np.arange(len(P), dtype=np.float64)
+    mean = float(np.dot(m, P))
+    var = float(np.dot(m * m, P)) - mean * mean
+    return var / mean
+
+
 # --------------------------------------------------------------------------
 # Adjoint gradient of F(rho) for parameters theta in (Delta, E, g0, kappa).
 #

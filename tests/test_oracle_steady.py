@@ -194,3 +194,37 @@ def test_dense_eta_uses_the_unmodified_liouvillian():
     assert r.eta < 1e-14
     lt_inf = np.abs(Lt).sum(axis=1).max()
     assert np.abs(Lt @ r.x).max() / (lt_inf * np.abs(r.x).max()) > 1e-4
+
+
+def test_phonon_distribution_thermal_closed_form():
+    """g0 = 0: the mechanics is the truncated thermal state, P(m) = r^m (1 - r) /
+    (1 - r^N_m), r = n_th / (1 + n_th) (exact under truncation by detailed
+    balance); its Fano factor follows from the same closed form."""
+    from oracle.steady import fano_factor, phonon_distribution
+
+    p = Params(3, 12, 1.0, -1.0, 0.5, 0.0, 0.2, 1e3, 1.5)
+    rho = steady_state_dense(p).rho
+    r = p.n_th / (1 + p.n_th)
+    m = np.arange(p.Nm)
+    P = r ** m * (1 - r) / (1 - r ** p.Nm)
+    np.testing.assert_allclose(phonon_distribution(p, rho), P, atol=1e-12)
+    mean = (m * P).sum()
+    F = ((m * m * P).sum() - mean ** 2) / mean
+    assert fano_factor(phonon_distribution(p, rho)) == pytest.approx(F, rel=1e-10)
+    # the distribution sums to Tr rho = 1, and its mean is <b^dag b>
+    assert phonon_distribution(p, rho).sum() == pytest.approx(1.0, abs=1e-13)
+    assert mean == pytest.approx(observables(p, rho)["n_b"], rel=1e-11)
+
+
+def test_fano_factor_of_a_fock_and_a_poisson_distribution():
+    from oracle.steady import fano_factor
+
+    P = np.zeros(8)
+    P[3] = 1.0
+    assert fano_factor(P) == pytest.approx(0.0, abs=1e-15)
+    lam = 2.0
+    k = np.arange(60)
+    from math import lgamma
+
+    Q = np.exp(k * np.log(lam) - lam - np.array([lgamma(x + 1) for x in k]))
+    assert fano_factor(Q) == pytest.approx(1.0, rel=1e-12)
