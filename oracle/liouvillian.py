@@ -5,6 +5,12 @@ Test infrastructure only (see ``oracle/__init__.py``).
 * Hamiltonian, Eq. 1 (pump frame):
   H = -Delta a^dag a + omega_m b^dag b + g0 (b + b^dag) a^dag a + E (a + a^dag),
   with Gamma_m = omega_m / Q_m.
+* The variants named in Sec. VI (the conclusion) add, with X = b + b^dag,
+  a quadratic ("membrane in the middle") coupling g2 X^2 a^dag a and an
+  anharmonic oscillator term lam X^4; the paper prints neither coefficient,
+  so g2 and lam are named here.  X^2 and X^4 are the powers of the truncated
+  matrix X (the operator algebra done inside the N_m-level space), which
+  differ from the infinite-space operators only in the last levels.
 * Tensor order, Sec. III: a = a (x) I_b and b = I_a (x) b, so the Hilbert index
   of |c, m> is h = c * N_m + m and the dimension is n = N_c * N_m.
 * Lindblad form, Eq. 3:
@@ -46,6 +52,8 @@ class Params:
     E: float = 0.2
     Q_m: float = 1e3
     n_th: float = 0.5
+    g2: float = 0.0   # quadratic coupling g2 (b + b^dag)^2 a^dag a (Sec. VI)
+    lam: float = 0.0  # anharmonic term lam (b + b^dag)^4 (Sec. VI)
 
 
 def lowering(N: int) -> sp.csr_matrix:
@@ -70,9 +78,16 @@ def hamiltonian(p: Params) -> sp.csr_matrix:
     a, b = mode_operators(p.Nc, p.Nm)
     ad, bd = a.conj().T, b.conj().T
     num_a = ad @ a
+    X = b + bd
     H = (-p.Delta * num_a + p.omega_m * (bd @ b)
-         + p.g0 * ((b + bd) @ num_a) + p.E * (a + ad))
-    return sp.csr_matrix(H)
+         + p.g0 * (X @ num_a) + p.E * (a + ad))
+    if p.g2 != 0.0:
+        H = H + p.g2 * (X @ X @ num_a)
+    if p.lam != 0.0:
+        H = H + p.lam * (X @ X @ X @ X)
+    H = sp.csr_matrix(H)
+    H.eliminate_zeros()
+    return H
 
 
 def collapse_terms(p: Params, nth_floor: float = 0.0):

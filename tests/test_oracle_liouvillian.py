@@ -128,3 +128,57 @@ def test_bandwidth_profile_definition():
     assert bp["B"] == 5
     assert bp["up"] == 2 + 0 + 1 + 0
     assert bp["lp"] == 2 + 2 + 0 + 0
+
+
+# ---- Hamiltonian variants of Sec. VI: g2 (b + b^dag)^2 a^dag a and lam (b + b^dag)^4
+
+def _mech_block(p, c):
+    """The mechanical block <c, m| H |c, m'> of the oracle's H at cavity level c."""
+    from oracle.liouvillian import hamiltonian
+
+    H = hamiltonian(p).toarray()
+    s = slice(c * p.Nm, (c + 1) * p.Nm)
+    return H[s, s]
+
+
+def test_powers_of_position_match_the_ladder_closed_forms():
+    """Away from the cutoff, <m|X^2|m> = 2m + 1, <m+2|X^2|m> = sqrt((m+1)(m+2)),
+    <m|X^4|m> = 6m^2 + 6m + 3, <m+2|X^4|m> = (4m + 6) sqrt((m+1)(m+2)) and
+    <m+4|X^4|m> = sqrt((m+1)(m+2)(m+3)(m+4)) (X = b + b^dag, from b|m> =
+    sqrt(m)|m-1>): the g2 term at c = 1 and the lam term at c = 0."""
+    Nm = 24
+    base = dict(omega_m=0.0, Delta=0.0, kappa=0.1, g0=0.0, E=0.0, Q_m=1e3, n_th=0.0)
+    X2 = _mech_block(Params(2, Nm, **base, g2=1.0), 1)
+    X4 = _mech_block(Params(1, Nm, **base, lam=1.0), 0)
+    for m in range(Nm - 5):
+        assert X2[m, m] == pytest.approx(2 * m + 1, abs=1e-12)
+        assert X2[m + 2, m] == pytest.approx(np.sqrt((m + 1) * (m + 2)), abs=1e-12)
+        assert X2[m + 1, m] == 0 and X2[m + 3, m] == 0
+        assert X4[m, m] == pytest.approx(6 * m * m + 6 * m + 3, abs=1e-10)
+        assert X4[m + 2, m] == pytest.approx((4 * m + 6) * np.sqrt((m + 1) * (m + 2)), abs=1e-10)
+        assert X4[m + 4, m] == pytest.approx(np.sqrt((m + 1) * (m + 2) * (m + 3) * (m + 4)), abs=1e-10)
+        assert X4[m + 1, m] == 0 and X4[m + 3, m] == 0
+    # at the cutoff the truncated square lacks the b b^dag part: <N_m-1|X^2|N_m-1> = N_m - 1
+    assert X2[Nm - 1, Nm - 1] == pytest.approx(Nm - 1, abs=1e-12)
+
+
+def test_quadratic_coupling_shifts_the_mechanical_frequency():
+    """omega b^dag b + g2 c X^2 is a harmonic oscillator of frequency
+    Omega = sqrt(omega (omega + 4 g2 c)) with levels Omega (k + 1/2) - omega/2
+    (x = X / sqrt 2, p^2 + x^2 = 2 b^dag b + 1); the lowest levels of a wide
+    truncation reach them.  The cavity term -Delta c is a constant shift."""
+    Nm, g2, Delta = 160, 0.15, -0.4
+    p = Params(3, Nm, omega_m=1.0, Delta=Delta, kappa=0.1, g0=0.0, E=0.0, Q_m=1e3, n_th=0.0, g2=g2)
+    for c in (1, 2):
+        ev = np.linalg.eigvalsh(_mech_block(p, c))[:6]
+        Om = np.sqrt(1.0 * (1.0 + 4 * g2 * c))
+        ref = Om * (np.arange(6) + 0.5) - 0.5 - Delta * c
+        np.testing.assert_allclose(ev, ref, rtol=0, atol=1e-9)
+
+
+def test_variants_enter_the_superoperator_columns():
+    """The Kronecker-form L with both variants on against dense products on E_ij."""
+    p = Params(3, 6, **TINY, g2=0.07, lam=0.01)
+    L = liouvillian(p).toarray()
+    for k in range(0, L.shape[0], 7):
+        np.testing.assert_allclose(L[:, k], superoperator_column(p, k), rtol=0, atol=1e-13)

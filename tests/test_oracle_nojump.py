@@ -19,6 +19,7 @@ CASES = [
     Params(3, 4, 1.0, -1.0, 0.5, 0.3, 0.2, 1e3, 0.5),
     Params(2, 5, 1.0, 0.7, 0.3, 0.9, 0.4, 1e2, 2.0),
     Params(4, 3, 1.0, -2.0, 0.4, 0.8, 0.2, 1e3, 0.0),  # n_th = 0, floored
+    Params(3, 6, 1.0, -1.0, 0.5, 0.3, 0.2, 1e3, 0.5, g2=0.05, lam=0.01),  # Sec. VI variants
 ]
 
 
