@@ -39,6 +39,24 @@ def permute_symmetric(A: sp.csr_matrix, perm: np.ndarray) -> sp.csr_matrix:
     return B
 
 
+def equilibrate(A: sp.csr_matrix):
+    """Row and column scalings (r, c) of the equilibration step that the
+    iLUTP of Sec. II performs as SuperLU runs it, before it factors: r_i =
+    1 / max_j |a_ij|, then c_j = 1 / max_i |r_i a_ij|, so that every row of
+    diag(r) A and every column of diag(r) A diag(c) has largest modulus 1 (a
+    row of the latter has largest modulus >= 1).  A row or column without
+    entries keeps the scale 1.  The factors are then those of
+    diag(r) A diag(c), and the preconditioner is M^{-1} = diag(c) (L U)^{-1}
+    diag(r)."""
+    A = sp.csr_matrix(A)
+    absA = abs(A)
+    rmax = absA.max(axis=1).toarray().ravel()
+    r = np.where(rmax > 0, 1.0 / np.where(rmax > 0, rmax, 1.0), 1.0)
+    cmax = (sp.diags(r) @ absA).max(axis=0).toarray().ravel()
+    c = np.where(cmax > 0, 1.0 / np.where(cmax > 0, cmax, 1.0), 1.0)
+    return r, c
+
+
 @dataclass
 class ILUFactors:
     n: int

@@ -25,7 +25,7 @@ import scipy.sparse as sp
 
 from .gmres import gmres_right
 from .liouvillian import Params, augmented, diagonal_positions, mode_operators
-from .reorder_factor import ilut, permute_symmetric, rcm_permutation
+from .reorder_factor import equilibrate, ilut, permute_symmetric, rcm_permutation
 
 
 def rho_from_vec(x: np.ndarray, n: int) -> np.ndarray:
@@ -71,15 +71,23 @@ def steady_state_dense(p: Params, trace_mode: str = "replace", nth_floor: float 
 
 def steady_state_iterative(p: Params, trace_mode: str = "replace", nth_floor: float = 1e-15,
                            droptol: float = 1e-4, fill: float = 20.0, restart: int = 50,
-                           rtol: float = 1e-14, max_iterations: int = 5000) -> SteadyResult:
-    """RCM -> ILUT -> right-preconditioned GMRES(restart) on L~ (Sec. III-IV)."""
+                           rtol: float = 1e-14, max_iterations: int = 5000,
+                           equilibrated: bool = False) -> SteadyResult:
+    """RCM -> ILUT -> right-preconditioned GMRES(restart) on L~ (Sec. III-IV);
+    equilibrated=True factors diag(r) A diag(c) (``equilibrate``) instead."""
     t0 = time.perf_counter()
     Lt, b, w, L = augmented(p, trace_mode, nth_floor)
     perm = rcm_permutation(Lt)
     A = permute_symmetric(Lt, perm)
-    F = ilut(A, droptol, fill)
+    if equilibrated:
+        r, c = equilibrate(A)
+        F = ilut(sp.diags(r) @ A @ sp.diags(c), droptol, fill)
+        precond = lambda v: c * F.solve(r * v)  # noqa: E731
+    else:
+        F = ilut(A, droptol, fill)
+        precond = F.solve
     t1 = time.perf_counter()
-    res = gmres_right(lambda v: A @ v, F.solve, b[perm], restart=restart, rtol=rtol,
+    res = gmres_right(lambda v: A @ v, precond, b[perm], restart=restart, rtol=rtol,
                       max_iterations=max_iterations)
     x = np.empty_like(res.x)
     x[perm] = res.x

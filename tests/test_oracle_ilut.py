@@ -121,3 +121,61 @@ def test_hand_worked_fill_cap_with_ties():
     np.testing.assert_allclose(F.L().toarray() - np.eye(6), Lx, atol=1e-15)
     np.testing.assert_allclose(F.U().toarray(), Ux, atol=1e-15)
     assert F.n_guarded == 0
+
+
+# ---- equilibration before the factorisation (the iLUTP of Sec. II as SuperLU runs it)
+
+def test_equilibration_hand_worked():
+    """r_i = 1/max_j |a_ij| = (1/4, 2, 1/8); diag(r) A = [[.5, -1, 0], [0, 1, .5],
+    [1, 0, .125i]] has column maxima (1, 1, .5), so c = (1, 1, 2)."""
+    from oracle.reorder_factor import equilibrate
+
+    A = sp.csr_matrix(np.array([[2, -4, 0], [0, 0.5, 0.25], [8, 0, 1j]], dtype=complex))
+    r, c = equilibrate(A)
+    np.testing.assert_array_equal(r, [0.25, 2.0, 0.125])
+    np.testing.assert_array_equal(c, [1.0, 1.0, 2.0])
+    B = (sp.diags(r) @ A @ sp.diags(c)).toarray()
+    np.testing.assert_array_equal(B, [[0.5, -1, 0], [0, 1, 1], [1, 0, 0.25j]])
+
+
+def test_equilibration_maxima_and_empty_lines():
+    from oracle.reorder_factor import equilibrate
+
+    rng = np.random.default_rng(9)
+    A = sp.random(60, 60, density=0.08, random_state=3, format="csr") * (1 + 1j)
+    A = sp.csr_matrix(A + sp.diags(rng.uniform(1e-3, 1e3, 60)))
+    A = sp.csr_matrix(sp.diags(10.0 ** rng.uniform(-6, 6, 60)) @ A)
+    r, c = equilibrate(A)
+    R = abs(sp.diags(r) @ A)
+    np.testing.assert_allclose(R.max(axis=1).toarray().ravel(), 1.0, rtol=1e-15)
+    B = abs(sp.diags(r) @ A @ sp.diags(c))
+    np.testing.assert_allclose(B.max(axis=0).toarray().ravel(), 1.0, rtol=1e-15)
+    assert (c >= 1.0).all()
+    # a diagonal matrix equilibrates to unit moduli with c = 1
+    D = sp.diags(np.array([3.0, -0.5j, 2 + 2j]), format="csr")
+    r, c = equilibrate(D)
+    np.testing.assert_allclose(r, [1 / 3, 2.0, 1 / np.sqrt(8)], rtol=1e-15)
+    np.testing.assert_array_equal(c, 1.0)
+    # an empty row and column keep the scale 1
+    E = sp.csr_matrix(np.array([[0, 0, 0], [0, 4.0, 0], [0, 0, 0]], dtype=complex))
+    r, c = equilibrate(E)
+    np.testing.assert_array_equal(r, [1.0, 0.25, 1.0])
+    np.testing.assert_array_equal(c, [1.0, 1.0, 1.0])
+
+
+def test_equilibrated_complete_lu_inverts_the_original_matrix():
+    """With no dropping, diag(c) (L U)^{-1} diag(r) v = A^{-1} v: the scalings are
+    applied on the right sides (a swapped or missing scaling fails)."""
+    from oracle.reorder_factor import equilibrate
+
+    rng = np.random.default_rng(4)
+    n = 40
+    A = sp.random(n, n, density=0.15, random_state=5, format="csr") * (2 - 1j) + sp.diags(rng.uniform(1, 2, n))
+    A = sp.csr_matrix(sp.diags(10.0 ** rng.uniform(-4, 4, n)) @ A @ sp.diags(10.0 ** rng.uniform(-3, 3, n)))
+    A.sort_indices()
+    r, c = equilibrate(A)
+    F = ilut(sp.diags(r) @ A @ sp.diags(c), 0.0, 2.0 * n)
+    v = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    x = c * F.solve(r * v)
+    ref = np.linalg.solve(A.toarray(), v)
+    np.testing.assert_allclose(x, ref, rtol=1e-9, atol=0)
