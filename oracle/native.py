@@ -53,6 +53,11 @@ def lib():
                                       ctypes.c_int64, _I64P, _I32P, _F64P,
                                       ctypes.c_int64, _I64P, _I32P, _F64P, _I64P]
             L.oracle_ilut.restype = ctypes.c_int
+            L.oracle_ilutp.argtypes = [ctypes.c_int64, _I64P, _I32P, _F64P,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int64, _I64P, _I32P, _F64P,
+                                       ctypes.c_int64, _I64P, _I32P, _F64P, _I32P, _I64P, _I64P]
+            L.oracle_ilutp.restype = ctypes.c_int
             for name in ("oracle_lsolve", "oracle_usolve", "oracle_uhsolve", "oracle_lhsolve"):
                 f = getattr(L, name)
                 f.argtypes = [ctypes.c_int64, _I64P, _I32P, _F64P, _F64P, _F64P]

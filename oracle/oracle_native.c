@@ -282,6 +282,192 @@ int oracle_ilut(int64_t n, const int64_t *ap, const int32_t *ai, const double *a
 }
 
 /* ------------------------------------------------------------------------ */
+/* ILUTP: ILUT with threshold column pivoting, the "P" of the iLUTP of      */
+/* Sec. II.  Row i is eliminated as in oracle_ilut, but in the order of the */
+/* current column positions: q[k] is the column at position k, qinv its     */
+/* inverse.  After the drop rule and the fill cap, if                        */
+/*   permtol * max |u_ij| (kept off-diagonal entries) > |u_ii|,              */
+/* the column of that largest entry (ties: the smallest position) takes     */
+/* position i and the old diagonal column takes its place.  The factors     */
+/* satisfy A Q ~ L U with (A Q)_{ik} = a_{i, q[k]}; L and U are returned in */
+/* position space (U rows diagonal first, then increasing position), and    */
+/* M^{-1} = Q U^{-1} L^{-1}.  permtol = 0 never pivots and gives exactly    */
+/* the factors of oracle_ilut.  Same capacities and return codes.           */
+/* ------------------------------------------------------------------------ */
+
+typedef struct { int32_t pos; double mag; int32_t col; } keepp_t;
+
+static int cmp_keepp(const void *pa, const void *pb) {
+    const keepp_t *a = (const keepp_t *)pa, *b = (const keepp_t *)pb;
+    if (a->mag != b->mag) return a->mag > b->mag ? -1 : 1; /* larger first */
+    return (a->pos > b->pos) - (a->pos < b->pos);          /* then smaller position */
+}
+
+static int cmp_keepp_pos(const void *pa, const void *pb) {
+    const keepp_t *a = (const keepp_t *)pa, *b = (const keepp_t *)pb;
+    return (a->pos > b->pos) - (a->pos < b->pos);
+}
+
+int oracle_ilutp(int64_t n, const int64_t *ap, const int32_t *ai, const double *ax_,
+                 double droptol, double fill, double permtol,
+                 int64_t cap_l, int64_t *lp, int32_t *li, double *lx_,
+                 int64_t cap_u, int64_t *up, int32_t *ui, double *ux_,
+                 int32_t *q, int64_t *n_guarded, int64_t *n_swaps) {
+    const cplx *ax = (const cplx *)ax_;
+    cplx *lx = (cplx *)lx_;
+    cplx *ux = (cplx *)ux_;
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    cplx *w = (cplx *)calloc(nn, sizeof(cplx));
+    unsigned char *present = (unsigned char *)calloc(nn, 1);
+    int32_t *cols = (int32_t *)malloc(sizeof(int32_t) * nn);
+    int32_t *heap = (int32_t *)malloc(sizeof(int32_t) * nn); /* positions < i */
+    int32_t *qinv = (int32_t *)malloc(sizeof(int32_t) * nn);
+    keepp_t *cand = (keepp_t *)malloc(sizeof(keepp_t) * nn);
+    if (!w || !present || !cols || !heap || !qinv || !cand) {
+        free(w); free(present); free(cols); free(heap); free(qinv); free(cand);
+        return -1;
+    }
+    for (int64_t k = 0; k < n; ++k) { q[k] = (int32_t)k; qinv[k] = (int32_t)k; }
+    *n_guarded = 0;
+    *n_swaps = 0;
+    lp[0] = 0;
+    up[0] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t nnz_i = ap[i + 1] - ap[i];
+        double row_inf = 0.0;
+        for (int64_t e = ap[i]; e < ap[i + 1]; ++e) {
+            double m = cabs(ax[e]);
+            if (m > row_inf) row_inf = m;
+        }
+        double tau = droptol * row_inf;
+        int64_t keep_cap = (int64_t)floor(fill * (double)nnz_i / 2.0);
+        if (keep_cap < 1) keep_cap = 1;
+
+        int64_t ncols = 0, hlen = 0;
+        for (int64_t e = ap[i]; e < ap[i + 1]; ++e) {
+            int32_t j = ai[e];
+            w[j] = ax[e];
+            present[j] = 1;
+            cols[ncols++] = j;
+            if (qinv[j] < i) heap_push(heap, &hlen, qinv[j]);
+        }
+        int32_t dcol = q[i];
+        if (!present[dcol]) {
+            w[dcol] = 0.0;
+            present[dcol] = 1;
+            cols[ncols++] = dcol;
+        }
+
+        /* eliminate with the rows at positions k < i, in increasing k */
+        while (hlen > 0) {
+            int32_t k = heap_pop(heap, &hlen);
+            int32_t ck = q[k];
+            cplx wk = w[ck] / ux[up[k]];
+            if (cabs(wk) < tau) {
+                w[ck] = 0.0;
+                continue;
+            }
+            w[ck] = wk;
+            for (int64_t e = up[k] + 1; e < up[k + 1]; ++e) {
+                int32_t j = ui[e]; /* a column label until the end */
+                if (!present[j]) {
+                    present[j] = 1;
+                    w[j] = 0.0;
+                    cols[ncols++] = j;
+                    if (qinv[j] < i) heap_push(heap, &hlen, qinv[j]);
+                }
+                w[j] -= wk * ux[e];
+            }
+        }
+
+        /* L part: positions < i */
+        int64_t nl = 0;
+        for (int64_t t = 0; t < ncols; ++t) {
+            int32_t j = cols[t];
+            if (qinv[j] < i) {
+                double m = cabs(w[j]);
+                if (w[j] != 0.0 && !(m < tau)) { cand[nl].pos = qinv[j]; cand[nl].mag = m; cand[nl].col = j; ++nl; }
+            }
+        }
+        if (nl > keep_cap) {
+            qsort(cand, (size_t)nl, sizeof(keepp_t), cmp_keepp);
+            nl = keep_cap;
+        }
+        qsort(cand, (size_t)nl, sizeof(keepp_t), cmp_keepp_pos);
+        if (lp[i] + nl > cap_l) return -2;
+        for (int64_t t = 0; t < nl; ++t) {
+            li[lp[i] + t] = cand[t].pos;
+            lx[lp[i] + t] = w[cand[t].col];
+        }
+        lp[i + 1] = lp[i] + nl;
+
+        /* U part: positions > i */
+        int64_t nu = 0;
+        for (int64_t t = 0; t < ncols; ++t) {
+            int32_t j = cols[t];
+            if (qinv[j] > i) {
+                double m = cabs(w[j]);
+                if (w[j] != 0.0 && !(m < tau)) { cand[nu].pos = qinv[j]; cand[nu].mag = m; cand[nu].col = j; ++nu; }
+            }
+        }
+        if (nu > keep_cap - 1) {
+            qsort(cand, (size_t)nu, sizeof(keepp_t), cmp_keepp);
+            nu = keep_cap - 1;
+        }
+        if (up[i] + 1 + nu > cap_u) return -2;
+        /* threshold pivoting among the kept entries */
+        int64_t best = -1;
+        for (int64_t t = 0; t < nu; ++t)
+            if (best < 0 || cand[t].mag > cand[best].mag ||
+                (cand[t].mag == cand[best].mag && cand[t].pos < cand[best].pos))
+                best = t;
+        if (best >= 0 && permtol * cand[best].mag > cabs(w[dcol])) {
+            int32_t newc = cand[best].col;
+            int32_t p = qinv[newc];
+            q[i] = newc; qinv[newc] = (int32_t)i;
+            q[p] = dcol; qinv[dcol] = p;
+            cand[best].col = dcol;
+            cand[best].pos = p;
+            cand[best].mag = cabs(w[dcol]);
+            if (w[dcol] == 0.0) { cand[best] = cand[nu - 1]; --nu; }
+            dcol = newc;
+            ++*n_swaps;
+        }
+        cplx piv = w[dcol];
+        double guard = 1e-14 * row_inf;
+        if (cabs(piv) < guard || piv == 0.0) {
+            piv = guard > 0.0 ? guard : 1e-300;
+            ++*n_guarded;
+        }
+        ui[up[i]] = dcol;
+        ux[up[i]] = piv;
+        for (int64_t t = 0; t < nu; ++t) {
+            ui[up[i] + 1 + t] = cand[t].col;
+            ux[up[i] + 1 + t] = w[cand[t].col];
+        }
+        up[i + 1] = up[i] + 1 + nu;
+
+        for (int64_t t = 0; t < ncols; ++t) {
+            w[cols[t]] = 0.0;
+            present[cols[t]] = 0;
+        }
+    }
+    /* U columns to positions, each row's off-diagonal part in increasing position */
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t b = up[i], e = up[i + 1];
+        ui[b] = (int32_t)i;
+        int64_t m = 0;
+        for (int64_t t = b + 1; t < e; ++t) { cand[m].pos = qinv[ui[t]]; cand[m].col = (int32_t)(t - b - 1); cand[m].mag = 0; ++m; }
+        qsort(cand, (size_t)m, sizeof(keepp_t), cmp_keepp_pos);
+        for (int64_t t = 0; t < m; ++t) ((cplx *)w)[t] = ux[b + 1 + cand[t].col];
+        for (int64_t t = 0; t < m; ++t) { ui[b + 1 + t] = cand[t].pos; ux[b + 1 + t] = w[t]; }
+        for (int64_t t = 0; t < m; ++t) w[t] = 0.0;
+    }
+    free(w); free(present); free(cols); free(heap); free(qinv); free(cand);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Triangular sweeps with the ILUT factors (the preconditioner solve of     */
 /* Eq. 6, M = L U) and with their conjugate transposes (M^H = U^H L^H).     */
 /* ------------------------------------------------------------------------ */

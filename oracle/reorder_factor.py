@@ -67,6 +67,8 @@ class ILUFactors:
     ui: np.ndarray
     ux: np.ndarray
     n_guarded: int
+    q: np.ndarray | None = None  # ILUTP: q[k] = column at position k (A Q ~ L U)
+    n_swaps: int = 0
 
     @property
     def nnz_l(self) -> int:
@@ -90,8 +92,25 @@ class ILUFactors:
         U.sort_indices()
         return U
 
-    # M^{-1} v and M^{-H} v with M = L U (the preconditioner of Eq. 6)
+    # M^{-1} v and M^{-H} v with M = L U (the preconditioner of Eq. 6), or
+    # M = L U Q^T with column pivoting: M^{-1} = Q U^{-1} L^{-1},
+    # M^{-H} = L^{-H} U^{-H} Q^T
     def solve(self, v: np.ndarray) -> np.ndarray:
+        x = self._solve(v)
+        if self.q is not None:
+            out = np.empty_like(x)
+            out[self.q] = x
+            return out
+        return x
+
+    def solve_h(self, v: np.ndarray) -> np.ndarray:
+        """M^{-H} v."""
+        v = np.asarray(v, dtype=np.complex128)
+        if self.q is not None:
+            v = v[self.q]
+        return self._solve_h(v)
+
+    def _solve(self, v: np.ndarray) -> np.ndarray:
         x = np.ascontiguousarray(v, dtype=np.complex128).copy()
         Lb = native.lib()
         xp = x.view(np.float64).ctypes.data_as(_F64P)
@@ -101,7 +120,7 @@ class ILUFactors:
                          self.ux.view(np.float64).ctypes.data_as(_F64P), xp, xp)
         return x
 
-    def solve_h(self, v: np.ndarray) -> np.ndarray:
+    def _solve_h(self, v: np.ndarray) -> np.ndarray:
         """(L U)^{-H} v = L^{-H} U^{-H} v."""
         x = np.ascontiguousarray(v, dtype=np.complex128).copy()
         Lb = native.lib()
@@ -143,3 +162,38 @@ def ilut(A: sp.csr_matrix, droptol: float, fill: float) -> ILUFactors:
     nl, nu = int(lp[-1]), int(up[-1])
     return ILUFactors(n, lp, li[:nl].copy(), lx[:nl].copy(), up, ui[:nu].copy(), ux[:nu].copy(),
                       int(ng[0]))
+
+
+def ilutp(A: sp.csr_matrix, droptol: float, fill: float, permtol: float) -> ILUFactors:
+    """ILUTP(d, p, permtol): ILUT with threshold column pivoting (the iLUTP of
+    Sec. II); see oracle_ilutp in oracle_native.c.  The factors satisfy
+    A Q ~ L U and solve() applies M^{-1} = Q U^{-1} L^{-1}."""
+    A = sp.csr_matrix(A)
+    A.sort_indices()
+    n = A.shape[0]
+    ap = np.ascontiguousarray(A.indptr, dtype=np.int64)
+    ai = np.ascontiguousarray(A.indices, dtype=np.int32)
+    ax = np.ascontiguousarray(A.data, dtype=np.complex128)
+    nnz_row = np.diff(ap)
+    cap_row = np.maximum(np.floor(fill * nnz_row / 2.0).astype(np.int64), 1)
+    cap = int(cap_row.sum()) + n
+    lp = np.zeros(n + 1, dtype=np.int64)
+    up = np.zeros(n + 1, dtype=np.int64)
+    li = np.zeros(cap, dtype=np.int32)
+    ui = np.zeros(cap, dtype=np.int32)
+    lx = np.zeros(cap, dtype=np.complex128)
+    ux = np.zeros(cap, dtype=np.complex128)
+    q = np.zeros(max(n, 1), dtype=np.int32)
+    ng = np.zeros(1, dtype=np.int64)
+    ns = np.zeros(1, dtype=np.int64)
+    rc = native.lib().oracle_ilutp(
+        n, native.ptr(ap, _I64P), native.ptr(ai, _I32P), ax.view(np.float64).ctypes.data_as(_F64P),
+        float(droptol), float(fill), float(permtol),
+        cap, native.ptr(lp, _I64P), native.ptr(li, _I32P), lx.view(np.float64).ctypes.data_as(_F64P),
+        cap, native.ptr(up, _I64P), native.ptr(ui, _I32P), ux.view(np.float64).ctypes.data_as(_F64P),
+        native.ptr(q, _I32P), native.ptr(ng, _I64P), native.ptr(ns, _I64P))
+    if rc != 0:
+        raise RuntimeError(f"oracle_ilutp failed ({rc})")
+    nl, nu = int(lp[-1]), int(up[-1])
+    return ILUFactors(n, lp, li[:nl].copy(), lx[:nl].copy(), up, ui[:nu].copy(), ux[:nu].copy(),
+                      int(ng[0]), q[:n].copy(), int(ns[0]))

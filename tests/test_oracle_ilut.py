@@ -179,3 +179,64 @@ def test_equilibrated_complete_lu_inverts_the_original_matrix():
     x = c * F.solve(r * v)
     ref = np.linalg.solve(A.toarray(), v)
     np.testing.assert_allclose(x, ref, rtol=1e-9, atol=0)
+
+
+# ---- ILUTP: threshold column pivoting (the "P" of the iLUTP of Sec. II)
+
+def test_ilutp_hand_worked_swap():
+    """A = [[1, 4], [2, 3]].  permtol 0.1: 0.1 * 4 < 1, no swap.  permtol 0.5:
+    0.5 * 4 > 1, so column 1 takes position 0 (q = [1, 0]), U row 0 = (4, 1);
+    row 1 in positions is (3, 2): l = 3/4 and u = 2 - (3/4) 1 = 5/4."""
+    from oracle.reorder_factor import ilutp
+
+    A = sp.csr_matrix(np.array([[1, 4], [2, 3]], dtype=complex))
+    F = ilutp(A, 0.0, 10.0, 0.1)
+    assert F.n_swaps == 0 and list(F.q) == [0, 1]
+    F = ilutp(A, 0.0, 10.0, 0.5)
+    assert F.n_swaps == 1 and list(F.q) == [1, 0]
+    np.testing.assert_allclose(F.U().toarray(), [[4, 1], [0, 1.25]], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(F.L().toarray(), [[1, 0], [0.75, 1]], rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_ilutp_without_pivoting_is_ilut(seed):
+    from oracle.reorder_factor import ilutp
+
+    rng = np.random.default_rng(seed)
+    A = diag_dominant(rng, 80, 0.06)
+    A = sp.csr_matrix(A + sp.random(80, 80, density=0.03, random_state=seed) * 5.0)
+    A.sort_indices()
+    for d, fill in ((0.0, 1e3), (1e-2, 3.0)):
+        F, G = ilut(A, d, fill), ilutp(A, d, fill, 0.0)
+        assert G.n_swaps == 0 and list(G.q) == list(range(80))
+        for a, b in ((F.lp, G.lp), (F.li, G.li), (F.up, G.up), (F.ui, G.ui)):
+            np.testing.assert_array_equal(a, b)
+        np.testing.assert_array_equal(F.lx, G.lx)
+        np.testing.assert_array_equal(F.ux, G.ux)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_ilutp_complete_factorisation_pivots_by_rows_of_u(seed):
+    """d = 0, no cap, permtol = 1: A Q = L U exactly, every U row has its
+    largest modulus on the diagonal, and M^{-1} = A^{-1}, also on a matrix
+    with zeros on the diagonal."""
+    from oracle.reorder_factor import ilutp
+
+    rng = np.random.default_rng(seed)
+    n = 30
+    A = sp.random(n, n, density=0.2, random_state=seed, format="csr") * (1 + 2j)
+    A = A + sp.csr_matrix((rng.uniform(1, 2, n), (np.arange(n), rng.permutation(n))), shape=(n, n))
+    A = sp.csr_matrix(A)
+    A.setdiag(0)
+    A.eliminate_zeros()
+    A.sort_indices()
+    F = ilutp(A, 0.0, 4.0 * n, 1.0)
+    assert F.n_guarded == 0
+    Ad = A.toarray()
+    LU = F.L().toarray() @ F.U().toarray()
+    np.testing.assert_allclose(LU, Ad[:, F.q], rtol=0, atol=1e-12 * np.abs(Ad).max())
+    U = F.U().toarray()
+    assert (np.abs(np.diag(U))[:, None] >= np.abs(np.triu(U, 1)) * (1 - 1e-15)).all()
+    v = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    np.testing.assert_allclose(F.solve(v), np.linalg.solve(Ad, v), rtol=1e-9)
+    np.testing.assert_allclose(F.solve_h(v), np.linalg.solve(Ad.conj().T, v), rtol=1e-9)
