@@ -199,8 +199,9 @@ def invariants(rho_dev, p):
 class NojumpStep:
     """One pass of the no-jump path: assemble, factor K, solve, observables."""
 
-    def __init__(self, w, precision, tol, rho_dev):
+    def __init__(self, w, precision, tol, rho_dev, restart=RESTART, eig32=True):
         self.w, self.precision, self.tol, self.rho_dev = w, precision, tol, rho_dev
+        self.restart, self.eig32 = restart, eig32
 
     def __call__(self):
         from paper_1411_4356_gb300 import api
@@ -209,14 +210,15 @@ class NojumpStep:
         h0 = time.perf_counter()
         A = api.build_liouvillian(p, w.trace_mode, w.nth_floor)
         h1 = time.perf_counter()
-        M = api.nojump_factor(p, nth_floor=w.nth_floor, eig32=True)
+        M = api.nojump_factor(p, nth_floor=w.nth_floor, eig32=self.eig32)
         h2 = time.perf_counter()
-        _, info = api.steady_state_solve_nojump(A, M, restart=RESTART, tol=self.tol, precision=self.precision,
-                                                rho_out=self.rho_dev, max_iters=2000)
+        _, info = api.steady_state_solve_nojump(A, M, restart=self.restart, tol=self.tol, precision=self.precision,
+                                                rho_out=self.rho_dev, max_iters=8000)
         obs = api.observables(p.Nc, p.Nm, self.rho_dev)
+        P, mean, second, fano = api.phonon_distribution(p.Nc, p.Nm, self.rho_dev)
         st = dict(N=A.N, nnz=A.nnz, iterations=info.iterations, cycles=info.cycles, eta=info.eta,
                   solve_s=info.seconds, build_s=h1 - h0, factor_s=h2 - h1, factor_phases=M.timings,
-                  tensor_cores=M.tensor_cores, min_abs_d=M.min_abs_d, obs=obs)
+                  tensor_cores=M.tensor_cores, min_abs_d=M.min_abs_d, obs=obs, P=P, fano=fano)
         M.free()
         A.free()
         return st
@@ -368,6 +370,25 @@ def run_omss(args):
                 "eta": st["eta"], "solve_s": st["solve_s"], "factor_s": st["factor_s"],
                 "precision": "FP64 flexible GMRES, TF32 no-jump products",
                 "parity": parity_vs(golden("mid_10x60_reference.json"), rho_mid, nm)}
+            # the paper's application (Sec. V, Fig. 5): the c-CPT at 640,000 rows
+            from paper_1411_4356_gb300 import CCPT
+
+            nc = CCPT.params.Nc * CCPT.params.Nm
+            rho_cc = torch.empty(nc * nc, dtype=torch.complex128, device="cuda")
+            cstep = NojumpStep(CCPT, CCPT.precision, CCPT.tol, rho_cc, restart=CCPT.restart, eig32=False)
+            cstep()
+            dt, st = timed(cstep, stream, reps=2)
+            ref = golden("ccpt_5x160_reference.json")
+            extras["ccpt_5x160"] = {
+                "value": world / dt, "unit": "solves/s", "ms_per_step": dt * 1e3, "iterations": st["iterations"],
+                "eta": st["eta"], "tol": CCPT.tol, "solve_s": st["solve_s"], "factor_s": st["factor_s"],
+                "precision": "complex64 GMRES(120) in FP64 refinement, TF32 no-jump products",
+                "n_b": st["obs"][1], "fano": st["fano"],
+                "parity": None if ref is None else dict(
+                    parity_vs(ref, rho_cc, nc),
+                    max_abs_err_P=float(np.abs(st["P"] - np.array(ref["P"])).max()),
+                    oracle_fano=ref["fano"], oracle_eta=ref["eta"])}
+            del rho_cc
             api.profile(True)
             dt, st = timed(lambda: ilu_step(MID, rho_mid, args.tol), stream)
             sp_ms, sp_n = api.profile_read(api.PROF_SPLIT)

@@ -58,10 +58,15 @@ typedef enum {
 } om_status;
 
 /* Parameters of Eq. 1 and Eq. 3 (units of omega_m) and the Fock cutoffs of
- * Sec. III.  Gamma_m = omega_m / Q_m. */
+ * Sec. III.  Gamma_m = omega_m / Q_m.  g2 and lam add the Hamiltonian variants
+ * that Sec. VI names, g2 (b + b^dag)^2 a^dag a (quadratic, "membrane in the
+ * middle" coupling) and lam (b + b^dag)^4 (anharmonic oscillator term), with
+ * the powers of b + b^dag taken in the truncated N_m-level space; zero gives
+ * Eq. 1 exactly.  Every entry point that takes om_params honours them. */
 typedef struct {
     int32_t Nc, Nm;
     double omega_m, Delta, kappa, g0, E, Q_m, n_th;
+    double g2, lam;
 } om_params;
 
 typedef struct {
@@ -162,7 +167,12 @@ om_status om_permute(const om_matrix *A, void *stream, int32_t *perm_dev, om_mat
  * flags bit 0: add the moduli of the entries dropped from row i to |u_ii|
  * (diagonal compensation); bit 1: also store the conjugate transposes U^H,
  * L^H needed by the adjoint; bit 2: also keep complex128 sweep data (the
- * sweeps use complex64 otherwise).  Rows are factored in parallel on the
+ * sweeps use complex64 otherwise); bit 3: equilibrate first, as the iLUTP of
+ * Sec. II does when SuperLU runs it -- r_i = 1 / max_j |a_ij|, then
+ * c_j = 1 / max_i |r_i a_ij| -- and factor diag(r) A diag(c) (the drop rule
+ * then reads the scaled rows); every application of the handle is
+ * M^{-1} = diag(c) (L U)^{-1} diag(r) (M^{-H} = diag(r) (L U)^{-H} diag(c)).
+ * Rows are factored in parallel on the
  * host cores (OMSS_ILU_THREADS caps the thread count); the factors are
  * identical to those of the serial row order.  On the device the factors are
  * stored in the tiled form of the sweeps: per tile of 32 rows, the dense
@@ -170,6 +180,28 @@ om_status om_permute(const om_matrix *A, void *stream, int32_t *perm_dev, om_mat
  * Errors: OM_EINVAL, OM_ENOMEM. */
 om_status om_ilu_factor(const om_matrix *A_rcm, double droptol, double fill, int32_t flags,
                         void *stream, om_ilu **out);
+
+/* ILUTP(d, p, permtol): the ILUT above with threshold column pivoting, the
+ * "P" of the iLUTP of Sec. II.  Rows are eliminated in the order of the
+ * current column positions; after the drop rule and the fill cap, if
+ * permtol * (largest kept off-diagonal modulus of U row i) > |u_ii|, that
+ * entry's column moves to position i (ties: the smaller position) and the
+ * old diagonal column takes its place.  The factors satisfy A Q ~ L U; every
+ * application of the handle is M^{-1} = Q U^{-1} L^{-1} (with the
+ * equilibration scalings of flag bit 3 outside).  permtol in (0, 1] (0.1
+ * keeps the diagonal while it is at least a tenth of the largest entry, the
+ * threshold SuperLU's incomplete LU uses); flags as for om_ilu_factor except
+ * bit 0 (compensation), which is rejected.  The rows are factored one after
+ * the other on one host core (the pivots make row i depend on every earlier
+ * pivot).  Errors: OM_EINVAL, OM_ENOMEM. */
+om_status om_ilutp_factor(const om_matrix *A_rcm, double droptol, double fill, double permtol, int32_t flags,
+                          void *stream, om_ilu **out);
+
+/* Pivoting of a factor: *pivoted = 1 for an om_ilutp_factor handle, the
+ * number of column swaps, and the column at each position (HOST int32[N],
+ * the identity without pivoting; synchronises the stream).  Any out pointer
+ * may be NULL.  Errors: OM_EINVAL, OM_ECUDA. */
+om_status om_ilu_pivots(const om_ilu *M, int32_t *pivoted, int64_t *n_swaps, int32_t *colperm_host, void *stream);
 
 /* Statistics of a factorisation (any out pointer may be NULL). */
 om_status om_ilu_info(const om_ilu *M, int64_t *nnz_l, int64_t *nnz_u, int64_t *n_guarded,
@@ -294,8 +326,8 @@ om_status om_spmv(const om_matrix *A, const double *x, double *y, void *stream);
  * entries, x and y must not alias.  Errors: OM_EINVAL (NULL, aliasing or a
  * permuted matrix), OM_ECUDA. */
 om_status om_liouvillian_apply(const om_matrix *A, const double *x, double *y, void *stream);
-/* z = (L U)^{-1} v, or (L U)^{-H} v, with DEVICE c128[N] vectors (z and v may
- * alias).  flags bit 0: sweep with the complex128 data (the factor must have
+/* z = M^{-1} v, or M^{-H} v, with DEVICE c128[N] vectors (z and v may alias);
+ * M = L U, or diag(r)^{-1} L U diag(c)^{-1} for equilibrated factors.  flags bit 0: sweep with the complex128 data (the factor must have
  * been built with it), else complex64; bit 1: apply the conjugate transpose
  * (the factor must keep the transposes); bit 2: run the complex64 sweeps in
  * one thread block even where the split sweep over all SMs applies (the two
@@ -304,8 +336,8 @@ om_status om_liouvillian_apply(const om_matrix *A, const double *x, double *y, v
 om_status om_ilu_apply(const om_ilu *M, int32_t flags, const double *v, double *z,
                        void *stream);
 /* Sec. IV's estimate of how the preconditioner amplifies errors, read as
- * ||(L U)^{-1} e||_inf with e the vector of ones (one forward and one
- * backward sweep).  flags as for om_ilu_apply (bit 0: complex128 sweeps; bit
+ * ||M^{-1} e||_inf with e the vector of ones (one forward and one backward
+ * sweep, with the scalings of equilibrated factors).  flags as for om_ilu_apply (bit 0: complex128 sweeps; bit
  * 2: one-block sweeps; bit 1 is ignored).  out: HOST double.  A NaN or Inf
  * result marks an unstable factorisation.  Errors: OM_EINVAL, OM_ECUDA. */
 om_status om_ilu_condest(const om_ilu *M, int32_t flags, double *out, void *stream);
@@ -326,6 +358,13 @@ om_status om_ilu_condest(const om_ilu *M, int32_t flags, double *out, void *stre
  * streams, say) race.  Errors: OM_EINVAL, OM_ECUDA. */
 om_status om_ilu_apply_noalloc(const om_ilu *M, int32_t flags, const double *v, double *z,
                                void *stream);
+/* Phonon number distribution of Sec. V (Fig. 5): P[m] = <m| Tr_cavity(rho) |m>
+ * (HOST double[Nm]) of a DEVICE rho (c128 n x n column-major, n = Nc Nm), and
+ * moments (HOST double[3]) = <N_b>, <N_b^2> and the Fano factor
+ * F = <(Delta N_b)^2> / <N_b> (0 when <N_b> = 0).  Synchronises the stream.
+ * Errors: OM_EINVAL, OM_ECUDA. */
+om_status om_phonon_distribution(int32_t Nc, int32_t Nm, const double *rho_dev, double *P, double moments[3],
+                                 void *stream);
 /* <a^dag a>, <b^dag b> of a DEVICE rho (c128 n x n column-major); out HOST double[2]. */
 om_status om_observables(int32_t Nc, int32_t Nm, const double *rho_dev, double out[2],
                          void *stream);

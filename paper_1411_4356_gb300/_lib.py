@@ -15,7 +15,7 @@ c_i32, c_i64, c_dbl, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, cty
 
 class om_params(ctypes.Structure):
     _fields_ = [("Nc", c_i32), ("Nm", c_i32), ("omega_m", c_dbl), ("Delta", c_dbl), ("kappa", c_dbl),
-                ("g0", c_dbl), ("E", c_dbl), ("Q_m", c_dbl), ("n_th", c_dbl)]
+                ("g0", c_dbl), ("E", c_dbl), ("Q_m", c_dbl), ("n_th", c_dbl), ("g2", c_dbl), ("lam", c_dbl)]
 
 
 class om_build_opts(ctypes.Structure):
@@ -47,6 +47,8 @@ SIGNATURES = {
     "om_matrix_export": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),
     "om_permute": (c_i32, [c_vp, c_vp, c_vp, ctypes.POINTER(c_vp)]),
     "om_ilu_factor": (c_i32, [c_vp, c_dbl, c_dbl, c_i32, c_vp, ctypes.POINTER(c_vp)]),
+    "om_ilutp_factor": (c_i32, [c_vp, c_dbl, c_dbl, c_dbl, c_i32, c_vp, ctypes.POINTER(c_vp)]),
+    "om_ilu_pivots": (c_i32, [c_vp, ctypes.POINTER(c_i32), ctypes.POINTER(c_i64), c_vp, c_vp]),
     "om_ilu_info": (c_i32, [c_vp] + [ctypes.POINTER(c_i64)] * 5),
     "om_ilu_timings": (c_i32, [c_vp, ctypes.POINTER(c_dbl)]),
     "om_steady_state_solve": (c_i32, [c_vp, c_vp, c_vp, ctypes.POINTER(om_solve_opts), c_vp, c_vp,
@@ -73,6 +75,7 @@ SIGNATURES = {
     "om_ilu_apply_noalloc": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp]),
     "om_ilu_condest": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_dbl), c_vp]),
     "om_observables": (c_i32, [c_i32, c_i32, c_vp, ctypes.POINTER(c_dbl * 2), c_vp]),
+    "om_phonon_distribution": (c_i32, [c_i32, c_i32, c_vp, c_vp, ctypes.POINTER(c_dbl * 3), c_vp]),
     "om_kernel_launches": (c_i64, []),
     "om_profile": (c_i32, [c_i32]),
     "om_profile_read": (c_i32, [c_i32, ctypes.POINTER(c_dbl), ctypes.POINTER(c_i64)]),

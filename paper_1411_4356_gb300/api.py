@@ -76,7 +76,7 @@ def allocator_hook_calls() -> int:
 
 
 def to_om_params(p: SystemParams) -> om_params:
-    return om_params(p.Nc, p.Nm, p.omega_m, p.Delta, p.kappa, p.g0, p.E, p.Q_m, p.n_th)
+    return om_params(p.Nc, p.Nm, p.omega_m, p.Delta, p.kappa, p.g0, p.E, p.Q_m, p.n_th, p.g2, p.lam)
 
 
 class Matrix:
@@ -120,8 +120,9 @@ class Matrix:
 class ILU:
     """ILU factors handle (om_ilu)."""
 
-    def __init__(self, handle: int, nnz_a: int):
+    def __init__(self, handle: int, nnz_a: int, N: int = 0):
         self._h = ctypes.c_void_p(handle)
+        self.N = N
         vals = [ctypes.c_int64() for _ in range(5)]
         check(_lib.load().om_ilu_info(self._h, *[ctypes.byref(v) for v in vals]), "om_ilu_info")
         self.nnz_l, self.nnz_u, self.n_guarded, self.levels_l, self.levels_u = (v.value for v in vals)
@@ -169,16 +170,34 @@ def permute(A: Matrix, stream=None):
 
 
 def ilu_factor(A: Matrix, droptol: float, fill: float, compensate: bool = False, adjoint: bool = False,
-               fp64_sweeps: bool = False, stream=None) -> ILU:
+               fp64_sweeps: bool = False, equilibrate: bool = False, permtol: float = 0.0, stream=None) -> ILU:
     """Sec. II: ILUT(droptol, fill) of a permuted matrix; adjoint=True also keeps
     the conjugate-transposed factors for the adjoint sweeps, fp64_sweeps=True
-    the complex128 sweep data."""
+    the complex128 sweep data, equilibrate=True factors diag(r) A diag(c)
+    (row, then column equilibration), permtol > 0 adds threshold column
+    pivoting (ILUTP, om_ilutp_factor)."""
     lib = _lib.load()
     out = ctypes.c_void_p()
-    flags = (1 if compensate else 0) | (2 if adjoint else 0) | (4 if fp64_sweeps else 0)
-    check(lib.om_ilu_factor(A.handle, float(droptol), float(fill), flags,
-                            ctypes.c_void_p(_stream(stream)), ctypes.byref(out)), "om_ilu_factor")
-    return ILU(out.value, A.nnz)
+    flags = ((1 if compensate else 0) | (2 if adjoint else 0) | (4 if fp64_sweeps else 0)
+             | (8 if equilibrate else 0))
+    if permtol != 0:
+        check(lib.om_ilutp_factor(A.handle, float(droptol), float(fill), float(permtol), flags,
+                                  ctypes.c_void_p(_stream(stream)), ctypes.byref(out)), "om_ilutp_factor")
+    else:
+        check(lib.om_ilu_factor(A.handle, float(droptol), float(fill), flags,
+                                ctypes.c_void_p(_stream(stream)), ctypes.byref(out)), "om_ilu_factor")
+    return ILU(out.value, A.nnz, A.N)
+
+
+def ilu_pivots(M: ILU, stream=None):
+    """(pivoted, number of column swaps, q as a numpy int32 array: the column at each position)."""
+    piv = ctypes.c_int32()
+    ns = ctypes.c_int64()
+    q = np.empty(M.N, dtype=np.int32)
+    check(_lib.load().om_ilu_pivots(M.handle, ctypes.byref(piv), ctypes.byref(ns),
+                                    q.ctypes.data_as(ctypes.c_void_p), ctypes.c_void_p(_stream(stream))),
+          "om_ilu_pivots")
+    return bool(piv.value), int(ns.value), q
 
 
 @dataclass
@@ -356,8 +375,9 @@ def liouvillian_apply(A: Matrix, x: torch.Tensor, stream=None) -> torch.Tensor:
 
 def ilu_apply(M: ILU, v: torch.Tensor, conj_transpose: bool = False, fp64: bool = False,
               single_block: bool = False, stream=None) -> torch.Tensor:
-    """z = (L U)^{-1} v (or (L U)^{-H} v); fp64 selects the complex128 sweeps,
-    single_block keeps the complex64 sweeps in one thread block."""
+    """z = M^{-1} v (or M^{-H} v), M = L U, or diag(r)^{-1} L U diag(c)^{-1} for
+    equilibrated factors; fp64 selects the complex128 sweeps, single_block
+    keeps the complex64 sweeps in one thread block."""
     z = torch.empty_like(v)
     flags = (1 if fp64 else 0) | (2 if conj_transpose else 0) | (4 if single_block else 0)
     check(_lib.load().om_ilu_apply(M.handle, flags, _ptr(v.contiguous()), _ptr(z),
@@ -366,7 +386,7 @@ def ilu_apply(M: ILU, v: torch.Tensor, conj_transpose: bool = False, fp64: bool 
 
 
 def ilu_condest(M: ILU, fp64: bool = False, single_block: bool = False, stream=None) -> float:
-    """||(L U)^{-1} e||_inf, e = ones (Sec. IV's stability estimate of the factors)."""
+    """||M^{-1} e||_inf, e = ones (Sec. IV's stability estimate of the factors)."""
     out = ctypes.c_double()
     flags = (1 if fp64 else 0) | (4 if single_block else 0)
     check(_lib.load().om_ilu_condest(M.handle, flags, ctypes.byref(out), ctypes.c_void_p(_stream(stream))),
@@ -381,6 +401,17 @@ def observables(Nc: int, Nm: int, rho: torch.Tensor, stream=None):
     check(_lib.load().om_observables(int(Nc), int(Nm), _ptr(flat), ctypes.byref(out),
                                      ctypes.c_void_p(_stream(stream))), "om_observables")
     return out[0], out[1]
+
+
+def phonon_distribution(Nc: int, Nm: int, rho: torch.Tensor, stream=None):
+    """(P[m] numpy array, <N_b>, <N_b^2>, Fano factor) of a CUDA rho (Sec. V, Fig. 5)."""
+    flat = rho.t().contiguous().view(-1) if rho.dim() == 2 else rho
+    P = np.empty(int(Nm), dtype=np.float64)
+    mom = (ctypes.c_double * 3)()
+    check(_lib.load().om_phonon_distribution(int(Nc), int(Nm), _ptr(flat), P.ctypes.data_as(ctypes.c_void_p),
+                                             ctypes.byref(mom), ctypes.c_void_p(_stream(stream))),
+          "om_phonon_distribution")
+    return P, mom[0], mom[1], mom[2]
 
 
 def kernel_launches() -> int:

@@ -14,6 +14,11 @@
 // rho_{i+N_m, j+N_m}, rho_{i+1, j+1} and rho_{i-1, j-1} respectively (3
 // entries).  Entries that are exactly zero are dropped.  Row 0 becomes the
 // trace row of Eq. 5 and is built on the host (it has n entries).
+//
+// The Hamiltonian variants of Sec. VI, g2 c X^2 + lam X^4 (X = b + b^dag in
+// the truncated space), act within a cavity level and join m to m, m +/- 2 and
+// m +/- 4: their bands are tabulated per Hilbert index (variant_bands) and add
+// up to 8 more entries to a row.
 #include <algorithm>
 #include <cmath>
 #include <memory>
@@ -30,9 +35,13 @@ struct Model {
     double omega_m, Delta, kappa, g0, E;
     double gam_down;  // Gamma_m (1 + n_th)
     double gam_up;    // Gamma_m n_th
+    // variant bands (3 n entries, host or device memory as the caller runs),
+    // NULL without variants; vband = the widest band present (0, 2 or 4)
+    const double *vt;
+    int32_t vband;
 };
 
-constexpr int kMaxRow = 13;
+constexpr int kMaxRow = 21;
 
 __host__ __device__ inline double h_diag(const Model &M, int c, int m) {
     return -M.Delta * c + M.omega_m * m;
@@ -61,12 +70,30 @@ __host__ __device__ int liouvillian_row(const Model &M, int64_t k, int64_t *cols
     // left term -i H_{i,l} rho_{l,j}: l = i - N_m, i - 1
     if (ci >= 1) put((i - M.Nm) + (int64_t)j * n, 0.0, -M.E * sqrt((double)ci));
     if (mi >= 1) put((i - 1) + (int64_t)j * n, 0.0, -M.g0 * ci * sqrt((double)mi));
+    // variant bands below the diagonal (l = i - d, then l = j - d)
+    for (int q = M.vband / 2; q >= 1; --q) {
+        const int d = 2 * q;
+        if (mi >= d) put((i - d) + (int64_t)j * n, 0.0, -M.vt[(int64_t)q * n + i - d]);
+    }
     // diagonal
     {
         double re = -0.5 * (M.kappa * (ci + cj) + M.gam_down * (mi + mj) +
                             M.gam_up * (bbdag(M, mi) + bbdag(M, mj)));
         double im = -(h_diag(M, ci, mi) - h_diag(M, cj, mj));
+        if (M.vband) im = -((h_diag(M, ci, mi) + M.vt[i]) - (h_diag(M, cj, mj) + M.vt[j]));
         put(k, re, im);
+    }
+    for (int q = 1; q <= M.vband / 2; ++q) {
+        const int d = 2 * q;
+        if (mi + d < M.Nm) put((i + d) + (int64_t)j * n, 0.0, -M.vt[(int64_t)q * n + i]);
+    }
+    for (int q = M.vband / 2; q >= 1; --q) {
+        const int d = 2 * q;
+        if (mj >= d) put(i + (int64_t)(j - d) * n, 0.0, M.vt[(int64_t)q * n + j - d]);
+    }
+    for (int q = 1; q <= M.vband / 2; ++q) {
+        const int d = 2 * q;
+        if (mj + d < M.Nm) put(i + (int64_t)(j + d) * n, 0.0, M.vt[(int64_t)q * n + j]);
     }
     if (mi + 1 < M.Nm) put((i + 1) + (int64_t)j * n, 0.0, -M.g0 * ci * sqrt((double)(mi + 1)));
     if (ci + 1 < M.Nc) put((i + M.Nm) + (int64_t)j * n, 0.0, -M.E * sqrt((double)(ci + 1)));
@@ -137,7 +164,7 @@ __global__ void diag_positions(int32_t n, int32_t *pos) {
 //   y_k = -i sum_l (H_il x_lj - x_il H_lj) + jumps + diagonal,
 // the imaginary couplings applied as i b x = (-b x.y, b x.x), the real jump
 // couplings as a x.  Row 0 (the trace row) is written by trace_row_apply.
-enum { S_HD = 0, S_DR, S_GM, S_GP, S_EM, S_EP, S_SM, S_SP, S_SC1, S_COUNT };
+enum { S_HD = 0, S_DR, S_GM, S_GP, S_EM, S_EP, S_SM, S_SP, S_SC1, S_V2, S_V4, S_COUNT };
 
 template <class R>
 struct StencilArgs {
@@ -147,6 +174,7 @@ struct StencilArgs {
     int64_t N;
     R kappa, gam_down, gam_up, w;
     int32_t trace_mode;
+    int32_t vband;         // widest variant band (0, 2 or 4); S_HD holds the variants' diagonal
 };
 
 template <class T>
@@ -161,7 +189,7 @@ struct CxOps<float2> {
 };
 
 // sum over the entries of row k >= 0 of L (no trace row)
-template <class T, class R>
+template <class T, class R, bool VARIANTS = false>
 __device__ inline T stencil_row(const StencilArgs<R> &a, int32_t k, const T *__restrict__ x) {
     const int32_t n = a.n, Nm = a.Nm;
     const int32_t i = k % n, j = k / n;
@@ -196,6 +224,14 @@ __device__ inline T stencil_row(const StencilArgs<R> &a, int32_t k, const T *__r
     if (mj + 1 < Nm) imag_c(tab(S_GP, j), x[k + n]);
     if (cj >= 1) imag_c(tab(S_EM, j), x[k - (int64_t)Nm * n]);
     if (j + Nm < n) imag_c(tab(S_EP, j), x[k + (int64_t)Nm * n]);
+    // the variants' bands: H_{h, h+d} = V_d(h) = H_{h+d, h}, d = 2, 4
+    if (VARIANTS) for (int q = 1; q <= a.vband / 2; ++q) {
+        const int d = 2 * q, which = S_V2 + q - 1;
+        if (mi >= d) imag_c(-tab(which, i - d), x[k - d]);
+        if (mi + d < Nm) imag_c(-tab(which, i), x[k + d]);
+        if (mj >= d) imag_c(tab(which, j - d), x[k - (int64_t)d * n]);
+        if (mj + d < Nm) imag_c(tab(which, j), x[k + (int64_t)d * n]);
+    }
     // jumps: b^dag rho b -> x_{i-1, j-1}; b rho b^dag -> x_{i+1, j+1}; a rho a^dag -> x_{i+N_m, j+N_m}
     if (mi >= 1 && mj >= 1) real_c(a.gam_up * tab(S_SM, i) * tab(S_SM, j), x[k - 1 - n]);
     if (mi + 1 < Nm && mj + 1 < Nm) real_c(a.gam_down * tab(S_SP, i) * tab(S_SP, j), x[k + 1 + n]);
@@ -206,11 +242,11 @@ __device__ inline T stencil_row(const StencilArgs<R> &a, int32_t k, const T *__r
     return out;
 }
 
-template <class T, class R>
+template <class T, class R, bool VARIANTS>
 __global__ void __launch_bounds__(256) stencil_apply(StencilArgs<R> a, const T *__restrict__ x, T *__restrict__ y) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x + 1; k < a.N; k += stride)
-        y[k] = stencil_row<T, R>(a, (int32_t)k, x);
+        y[k] = stencil_row<T, R, VARIANTS>(a, (int32_t)k, x);
 }
 
 // y_0: w Tr(x) (replace mode) or (row 0 of L) x + w Tr(x) (add mode), one
@@ -237,7 +273,7 @@ __global__ void trace_row_apply(StencilArgs<R> a, const T *__restrict__ x, T *__
         out.x = a.w * s0;
         out.y = a.w * s1;
         if (a.trace_mode == 1) {
-            const T r = stencil_row<T, R>(a, 0, x);
+            const T r = a.vband ? stencil_row<T, R, true>(a, 0, x) : stencil_row<T, R, false>(a, 0, x);
             out.x += r.x;
             out.y += r.y;
         }
@@ -260,10 +296,14 @@ void launch_stencil(const om_matrix &A, const R *tab, const T *x, T *y, cudaStre
     a.gam_up = (R)(Gm * A.nth_eff);
     a.w = (R)A.w;
     a.trace_mode = A.trace_mode;
+    a.vband = A.vband;
     const int64_t need = (A.N + 255) / 256;
     const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 16));
     ProfScope prof(PROF_STENCIL, s);
-    stencil_apply<T, R><<<blocks, 256, 0, s>>>(a, x, y);
+    if (a.vband)
+        stencil_apply<T, R, true><<<blocks, 256, 0, s>>>(a, x, y);
+    else
+        stencil_apply<T, R, false><<<blocks, 256, 0, s>>>(a, x, y);
     note_launch();
     trace_row_apply<T, R><<<1, 256, 0, s>>>(a, x, y);
     note_launch();
@@ -278,7 +318,9 @@ void build_stencil_tables(const Model &M, std::vector<double> &t, std::vector<in
     for (int h = 0; h < n; ++h) {
         const int c = h / M.Nm, m = h % M.Nm;
         cm[h] = (c << 16) | m;
-        t[(size_t)S_HD * n + h] = h_diag(M, c, m);
+        t[(size_t)S_HD * n + h] = h_diag(M, c, m) + (M.vband ? M.vt[h] : 0.0);
+        t[(size_t)S_V2 * n + h] = M.vband ? M.vt[(size_t)n + h] : 0.0;
+        t[(size_t)S_V4 * n + h] = M.vband ? M.vt[(size_t)2 * n + h] : 0.0;
         t[(size_t)S_DR * n + h] = M.kappa * c + M.gam_down * m + M.gam_up * bbdag(M, m);
         t[(size_t)S_GM * n + h] = M.g0 * c * std::sqrt((double)m);
         t[(size_t)S_GP * n + h] = M.g0 * c * std::sqrt((double)(m + 1));
@@ -291,6 +333,61 @@ void build_stencil_tables(const Model &M, std::vector<double> &t, std::vector<in
 }
 
 }  // namespace
+
+// Banded products of the truncated X = b + b^dag (X_{m, m+1} = X_{m+1, m} =
+// sqrt(m+1)): X^2 = X X, X^4 = X^2 X^2, each entry summed over the
+// intermediate levels inside the N_m-level space.  v[q n + h] for
+// h = c N_m + m is (g2 c X^2 + lam X^4)_{m, m + 2q}, q = 0, 1, 2; returns the
+// widest band present.
+int variant_bands(const om_params &p, std::vector<double> &v) {
+    const int Nm = p.Nm, n = p.Nc * p.Nm;
+    if (p.g2 == 0.0 && p.lam == 0.0) {
+        v.clear();
+        return 0;
+    }
+    // band storage: B[m * (2w+1) + (e + w)] = M_{m, m+e}
+    auto X = [&](int m, int e) -> double {
+        const int l = m + e;
+        if (l < 0 || l >= Nm || (e != 1 && e != -1)) return 0.0;
+        return std::sqrt((double)std::max(m, l));
+    };
+    std::vector<double> X2((size_t)Nm * 5, 0.0), X4((size_t)Nm * 9, 0.0);
+    for (int m = 0; m < Nm; ++m)
+        for (int e = -2; e <= 2; ++e) {
+            double acc = 0.0;
+            for (int f = -1; f <= 1; f += 2) {
+                const int l = m + f;
+                if (l < 0 || l >= Nm) continue;
+                acc += X(m, f) * X(l, e - f);
+            }
+            X2[(size_t)m * 5 + (e + 2)] = acc;
+        }
+    auto x2 = [&](int m, int e) -> double {
+        if (m < 0 || m >= Nm || e < -2 || e > 2 || m + e < 0 || m + e >= Nm) return 0.0;
+        return X2[(size_t)m * 5 + (e + 2)];
+    };
+    for (int m = 0; m < Nm; ++m)
+        for (int e = -4; e <= 4; ++e) {
+            double acc = 0.0;
+            for (int f = -2; f <= 2; ++f) {
+                const int l = m + f;
+                if (l < 0 || l >= Nm) continue;
+                acc += x2(m, f) * x2(l, e - f);
+            }
+            X4[(size_t)m * 9 + (e + 4)] = acc;
+        }
+    v.assign((size_t)3 * n, 0.0);
+    for (int h = 0; h < n; ++h) {
+        const int c = h / Nm, m = h % Nm;
+        for (int q = 0; q <= 2; ++q) {
+            const int d = 2 * q;
+            if (m + d >= Nm) continue;
+            const double q2 = q <= 1 ? X2[(size_t)m * 5 + (d + 2)] : 0.0;
+            v[(size_t)q * n + h] = p.g2 * c * q2 + p.lam * X4[(size_t)m * 9 + (d + 4)];
+        }
+    }
+    return p.lam != 0.0 ? 4 : 2;
+}
 
 void liouvillian_apply_c128(const om_matrix &A, const double2 *x, double2 *y, cudaStream_t s) {
     launch_stencil<double2, double>(A, A.stab.p, x, y, s);
@@ -347,6 +444,10 @@ extern "C" om_status om_build_liouvillian(const om_params *params, const om_buil
         const double Gm = p.omega_m / p.Q_m;
         M.gam_down = Gm * (1.0 + nth);
         M.gam_up = Gm * nth;
+        OM_REQUIRE(std::isfinite(p.g2) && std::isfinite(p.lam), "g2 and lam must be finite");
+        std::vector<double> vt_host;
+        M.vband = variant_bands(p, vt_host);
+        M.vt = M.vband ? vt_host.data() : nullptr;
 
         auto A = std::make_unique<om_matrix>();
         A->owner_stream = s;
@@ -355,6 +456,7 @@ extern "C" om_status om_build_liouvillian(const om_params *params, const om_buil
         A->params = p;
         A->trace_mode = opts->trace_mode;
         A->nth_eff = nth;
+        A->vband = M.vband;
         // w = mean of diag(L) (Sec. IV) in closed form: the mean of
         // -(1/2) sum_O gamma_O [(O^dag O)_ii + (O^dag O)_jj] over all (i, j) is
         // -(1/n) sum_O gamma_O Tr(O^dag O) with the truncated traces
@@ -402,9 +504,17 @@ extern "C" om_status om_build_liouvillian(const om_params *params, const om_buil
         DBuf<double> normbits;
         normbits.alloc(1, s);
         OM_CUDA_TRY(cudaMemsetAsync(normbits.p, 0, sizeof(double), s));
+        DBuf<double> vt_dev;  // the variant bands for the device rows
+        Model Md = M;
+        if (M.vband) {
+            vt_dev.alloc(vt_host.size(), s);
+            OM_CUDA_TRY(cudaMemcpyAsync(vt_dev.p, vt_host.data(), sizeof(double) * vt_host.size(),
+                                        cudaMemcpyHostToDevice, s));
+            Md.vt = vt_dev.p;
+        }
         const int T = 256;
         const unsigned blocks = (unsigned)((N + T - 1) / T);
-        count_rows<<<blocks, T, 0, s>>>(M, N, counts.p, normbits.p); omss::note_launch();
+        count_rows<<<blocks, T, 0, s>>>(Md, N, counts.p, normbits.p); omss::note_launch();
         OM_CHECK_LAUNCH();
         int64_t c0count = (int64_t)tcol.size();
         OM_CUDA_TRY(cudaMemcpyAsync(counts.p, &c0count, sizeof(int64_t), cudaMemcpyHostToDevice, s));
@@ -420,7 +530,7 @@ extern "C" om_status om_build_liouvillian(const om_params *params, const om_buil
         A->norm_inf = norm;
         A->col.alloc(nnz, s);
         A->val.alloc(nnz, s);
-        fill_rows<<<blocks, T, 0, s>>>(M, N, A->rowptr.p, A->col.p, A->val.p); omss::note_launch();
+        fill_rows<<<blocks, T, 0, s>>>(Md, N, A->rowptr.p, A->col.p, A->val.p); omss::note_launch();
         OM_CHECK_LAUNCH();
         OM_CUDA_TRY(cudaMemcpyAsync(A->col.p, tcol.data(), sizeof(int32_t) * tcol.size(),
                                     cudaMemcpyHostToDevice, s));
@@ -453,6 +563,7 @@ extern "C" om_status om_build_liouvillian(const om_params *params, const om_buil
         counts.release(s);
         scratch.release(s);
         normbits.release(s);
+        vt_dev.release(s);
         OM_CUDA_TRY(cudaStreamSynchronize(s));  // host vectors above go out of scope
         *out = A.release();
     });

@@ -61,6 +61,8 @@ struct BSys {
     const int64_t *tpL, *tpU;
     const int32_t *colL, *colU;
     const float2 *valL, *valU, *GL, *GU;
+    const double *sr, *sc;  // equilibration scalings (NULL: none)
+    const int32_t *q;       // column permutation of pivoted factors (NULL: none)
     // state
     double2 *V, *Z, *wv, *x, *b;
     float2 *tmp;
@@ -90,7 +92,11 @@ __global__ void __launch_bounds__(kPrecondThreads, 1) b_precond(const BSys *sys,
     sm.status = status;
     sm.init();
     const double2 *v = S.V + (int64_t)j * S.N;
-    for (int64_t i = threadIdx.x; i < S.N; i += blockDim.x) S.tmp[i] = make_float2((float)v[i].x, (float)v[i].y);
+    // z_j = diag(c) (L U)^{-1} diag(r) v_j for equilibrated factors
+    for (int64_t i = threadIdx.x; i < S.N; i += blockDim.x) {
+        const double t = S.sr ? S.sr[i] : 1.0;
+        S.tmp[i] = make_float2((float)(t * v[i].x), (float)(t * v[i].y));
+    }
     __syncthreads();
     tsw::sweep_block<float2, kWin, kStages>(sm, S.N, S.ntL, 1, S.tpL, S.colL, S.valL, S.GL, S.tmp, S.tmp, 0);
     __syncthreads();
@@ -98,8 +104,11 @@ __global__ void __launch_bounds__(kPrecondThreads, 1) b_precond(const BSys *sys,
     __syncthreads();
     double2 *z = S.Z + (int64_t)j * S.N;
     for (int64_t i = threadIdx.x; i < S.N; i += blockDim.x) {
+        // pivoted factors: z = diag(c) Q (L U)^{-1} ..., the result scattered
         const float2 t = __ldcg(S.tmp + i);
-        z[i] = make_double2(t.x, t.y);
+        const int64_t c = S.q ? (int64_t)S.q[i] : i;
+        const double d = S.sc ? S.sc[c] : 1.0;
+        z[c] = make_double2(d * (double)t.x, d * (double)t.y);
     }
 }
 
@@ -453,6 +462,9 @@ void solve_lockstep(int32_t count, const om_matrix *const *A_rcm, const om_ilu *
             S.valU = F.U.val32.p;
             S.GL = F.L.G32.p;
             S.GU = F.U.G32.p;
+            S.sr = F.equilibrated ? F.scale_r.p : nullptr;
+            S.sc = F.equilibrated ? F.scale_c.p : nullptr;
+            S.q = F.pivoted ? F.colperm.p : nullptr;
             S.V = o.V.p;
             S.Z = o.Z.p;
             S.wv = o.wv.p;

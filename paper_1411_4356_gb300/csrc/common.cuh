@@ -164,6 +164,7 @@ struct om_matrix {
     om_params params{};
     int32_t trace_mode = 0;
     double nth_eff = 0;  // n_th actually used (after the floor)
+    int32_t vband = 0;   // widest band of the Sec. VI variants (0: Eq. 1 alone)
     double w = 0;        // Eq. 5 weight
     double norm_inf = 0; // ||L||_inf of the unmodified Liouvillian
     bool permuted = false;
@@ -242,6 +243,19 @@ struct om_ilu {
     double seconds[4] = {0, 0, 0, 0};  // host wall time: copy-out, ILUT, DAG depths, sweep layout + upload
     bool has_transpose = false;
     bool has_fp64 = false;
+    // equilibration (flag 8): the factors are those of diag(r) A diag(c), and
+    // M^{-1} = diag(c) (L U)^{-1} diag(r), M^{-H} = diag(r) (L U)^{-H} diag(c)
+    bool equilibrated = false;
+    omss::DBuf<double> scale_r, scale_c;  // N each
+    // threshold column pivoting (om_ilutp_factor): A Q ~ L U with the factors
+    // in position space, M^{-1} = Q U^{-1} L^{-1}; colperm[k] = column at
+    // position k, and work vectors for the permutation (allocated with the
+    // factors, so that an application allocates nothing)
+    bool pivoted = false;
+    int64_t n_swaps = 0;
+    omss::DBuf<int32_t> colperm;
+    omss::DBuf<double2> ptmp;   // only with complex128 sweep data
+    omss::DBuf<float2> ptmp32;
     cudaStream_t owner_stream = nullptr;
     ~om_ilu();
 };
@@ -295,6 +309,12 @@ namespace omss {
 void liouvillian_apply_c128(const om_matrix &A, const double2 *x, double2 *y, cudaStream_t s);
 void liouvillian_apply_c64(const om_matrix &A, const float2 *x, float2 *y, cudaStream_t s);
 
+// The Hamiltonian variants of Sec. VI per Hilbert index h = c N_m + m:
+// v[q n + h] = (g2 c X^2 + lam X^4)_{m, m + 2q}, q = 0, 1, 2, with X = b + b^dag
+// truncated to N_m levels (host).  Returns the widest band (0: no variants,
+// v left empty).
+int variant_bands(const om_params &p, std::vector<double> &v);
+
 // Kernel launchers implemented in the .cu files.
 void spmv_c128(const int64_t *rowptr, const int32_t *col, const double2 *val, int64_t N,
                const double2 *x, double2 *y, cudaStream_t s);
@@ -319,6 +339,13 @@ void precond_apply(const om_ilu &M, bool conj_transpose, bool fp64, const double
                    float2 *tmp32, cudaStream_t s, bool allow_split = true);
 void to_c64(const double2 *v, int64_t N, float2 *out, cudaStream_t s);
 void to_c128(const float2 *v, int64_t N, double2 *out, cudaStream_t s);
+// out_i = d_i v_i (d real, FP64; out may alias v): the equilibration scalings
+void scale_c128(const double *d, const double2 *v, int64_t N, double2 *out, cudaStream_t s);
+void scale_c64(const double *d, const float2 *v, int64_t N, float2 *out, cudaStream_t s);
+// complex64 (L U)^{-1} v (or (L U)^{-H} v) with the equilibration scalings of
+// the handle applied on both sides; v and z may alias
+void precond_apply_c64(const om_ilu &M, bool conj_transpose, const float2 *v, float2 *z, cudaStream_t s,
+                       bool allow_split = true);
 
 // Host-side helpers (permute.cu / ilu.cu)
 void csr_to_host(const om_matrix &A, std::vector<int64_t> &rp, std::vector<int32_t> &ci,

@@ -325,6 +325,244 @@ void ilut_host(int64_t N, const std::vector<int64_t> &arp, const std::vector<int
     guarded = S.guarded.load();
 }
 
+// ILUTP: ILUT with threshold column pivoting (the "P" of the iLUTP of
+// Sec. II).  Row i eliminates, in increasing position, the columns at
+// positions below i (q[k]: the column at position k, qinv its inverse), with
+// the drop rule and fill cap of ILUT.  Then, if permtol times the largest
+// modulus among the kept U entries exceeds |u_ii|, that entry's column takes
+// position i (ties: the smaller position) and the old diagonal column takes
+// its place.  The factors satisfy A Q ~ L U, (A Q)_{ik} = a_{i, q[k]}; L and
+// U come back in position space, M^{-1} = Q U^{-1} L^{-1}.
+//
+// Rows run in parallel as in ILUT, claimed in order.  A pivot at row j only
+// exchanges position j with a later one, so positions below the first
+// unfinished row are final and the others never move below it.  Row i reads
+// q[k] only once row k is done, scanning k upwards from the lowest position
+// its columns can hold, and decides its own pivot after row i - 1 is done:
+// rows finish in order, every row sees the same positions as in the serial
+// order, and the factors are those of the serial elimination.
+struct IlutpShared {
+    int64_t N;
+    const std::vector<int64_t> *arp;
+    const std::vector<int32_t> *aci;
+    const std::vector<double2> *ava;
+    double droptol, fill, permtol;
+    std::vector<int64_t> slot;
+    std::vector<int32_t> lcnt, ucnt;
+    std::vector<int32_t> lci, uci;  // L: positions; U: column labels until the end
+    std::vector<cd> lva, uva;
+    std::vector<cd> diag;
+    std::unique_ptr<std::atomic<int32_t>[]> q, qinv;
+    std::unique_ptr<std::atomic<int>[]> done;
+    std::atomic<int64_t> finished{0};  // rows 0 .. finished-1 are done
+    std::atomic<int64_t> next{0};
+    std::atomic<int64_t> guarded{0}, swaps{0};
+};
+
+void ilutp_worker(IlutpShared &S) {
+    struct Cand {
+        int32_t pos, col;
+        double mag;
+    };
+    auto by_size = [](const Cand &a, const Cand &b) { return a.mag != b.mag ? a.mag > b.mag : a.pos < b.pos; };
+    auto by_pos = [](const Cand &a, const Cand &b) { return a.pos < b.pos; };
+    auto wait_done = [&](int64_t k) {
+        for (int spins = 0; !S.done[k].load(std::memory_order_acquire); ++spins)
+            if (spins > 64) std::this_thread::yield();
+    };
+    const int64_t N = S.N;
+    const auto &arp = *S.arp;
+    const auto &aci = *S.aci;
+    const auto &ava = *S.ava;
+    std::vector<cd> w(N, cd(0, 0));
+    std::vector<unsigned char> present(N, 0);
+    std::vector<int32_t> cols;
+    std::vector<Cand> lo, hi;
+    for (;;) {
+        const int64_t i = S.next.fetch_add(1, std::memory_order_relaxed);
+        if (i >= N) break;
+        const int64_t nnz_i = arp[i + 1] - arp[i];
+        double anorm = 0;
+        for (int64_t e = arp[i]; e < arp[i + 1]; ++e) anorm = std::max(anorm, std::abs(cd(ava[e].x, ava[e].y)));
+        const double tau = S.droptol * anorm;
+        int64_t cap = (int64_t)std::floor(S.fill * (double)nnz_i / 2.0);
+        if (cap < 1) cap = 1;
+        // positions below W are final; a column at a position >= W stays >= W
+        const int64_t W = std::min<int64_t>(S.finished.load(std::memory_order_acquire), i);
+        cols.clear();
+        int64_t plo = W;
+        for (int64_t e = arp[i]; e < arp[i + 1]; ++e) {
+            const int32_t c = aci[e];
+            w[c] = cd(ava[e].x, ava[e].y);
+            present[c] = 1;
+            cols.push_back(c);
+            const int32_t pc = S.qinv[c].load(std::memory_order_relaxed);
+            if (pc < W) plo = std::min<int64_t>(plo, pc);
+        }
+        for (int64_t k = plo; k < i; ++k) {
+            if (k >= W) wait_done(k);
+            const int32_t ck = S.q[k].load(std::memory_order_relaxed);
+            if (!present[ck] || w[ck] == cd(0, 0)) continue;
+            const cd m = w[ck] / S.diag[k];
+            if (std::abs(m) < tau) {
+                w[ck] = 0;
+                continue;
+            }
+            w[ck] = m;
+            const int64_t ub = S.slot[k], ue = ub + S.ucnt[k];
+            for (int64_t e = ub; e < ue; ++e) {
+                const int32_t c = S.uci[e];
+                if (!present[c]) {
+                    present[c] = 1;
+                    cols.push_back(c);
+                }
+                w[c] -= m * S.uva[e];
+            }
+        }
+        if (i > 0) wait_done(i - 1);  // every earlier pivot is in place
+        int32_t dcol = S.q[i].load(std::memory_order_relaxed);
+        if (!present[dcol]) {
+            present[dcol] = 1;
+            cols.push_back(dcol);
+        }
+        lo.clear();
+        hi.clear();
+        for (int32_t c : cols) {
+            const int32_t pc = S.qinv[c].load(std::memory_order_relaxed);
+            if (pc == i || w[c] == cd(0, 0)) continue;
+            const double mg = std::abs(w[c]);
+            if (mg < tau) continue;
+            (pc < i ? lo : hi).push_back({pc, c, mg});
+        }
+        if ((int64_t)lo.size() > cap) {
+            std::nth_element(lo.begin(), lo.begin() + cap, lo.end(), by_size);
+            lo.resize(cap);
+        }
+        std::sort(lo.begin(), lo.end(), by_pos);
+        if ((int64_t)hi.size() > cap - 1) {
+            std::nth_element(hi.begin(), hi.begin() + (cap - 1), hi.end(), by_size);
+            hi.resize(cap - 1);
+        }
+        int64_t best = -1;
+        for (int64_t t = 0; t < (int64_t)hi.size(); ++t)
+            if (best < 0 || hi[t].mag > hi[best].mag || (hi[t].mag == hi[best].mag && hi[t].pos < hi[best].pos))
+                best = t;
+        if (best >= 0 && S.permtol * hi[best].mag > std::abs(w[dcol])) {
+            const int32_t newc = hi[best].col, pnew = hi[best].pos;
+            S.q[i].store(newc, std::memory_order_relaxed);
+            S.qinv[newc].store((int32_t)i, std::memory_order_relaxed);
+            S.q[pnew].store(dcol, std::memory_order_relaxed);
+            S.qinv[dcol].store(pnew, std::memory_order_relaxed);
+            if (w[dcol] == cd(0, 0)) {
+                hi[best] = hi.back();
+                hi.pop_back();
+            } else {
+                hi[best] = {pnew, dcol, std::abs(w[dcol])};
+            }
+            dcol = newc;
+            S.swaps.fetch_add(1, std::memory_order_relaxed);
+        }
+        const int64_t base = S.slot[i];
+        for (size_t t = 0; t < lo.size(); ++t) {
+            S.lci[base + t] = lo[t].pos;
+            S.lva[base + t] = w[lo[t].col];
+        }
+        S.lcnt[i] = (int32_t)lo.size();
+        cd piv = w[dcol];
+        const double floor_ = 1e-14 * anorm;
+        if (std::abs(piv) < floor_ || piv == cd(0, 0)) {
+            piv = cd(floor_ > 0 ? floor_ : 1e-300, 0);
+            S.guarded.fetch_add(1, std::memory_order_relaxed);
+        }
+        S.diag[i] = piv;
+        for (size_t t = 0; t < hi.size(); ++t) {
+            S.uci[base + t] = hi[t].col;
+            S.uva[base + t] = w[hi[t].col];
+        }
+        S.ucnt[i] = (int32_t)hi.size();
+        S.done[i].store(1, std::memory_order_release);
+        S.finished.store(i + 1, std::memory_order_release);
+        for (int32_t c : cols) {
+            w[c] = cd(0, 0);
+            present[c] = 0;
+        }
+    }
+}
+
+void ilutp_host(int64_t N, const std::vector<int64_t> &arp, const std::vector<int32_t> &aci,
+                const std::vector<double2> &ava, double droptol, double fill, double permtol, HostTri &L,
+                HostTri &U, std::vector<cd> &diag, std::vector<int32_t> &q, int64_t &guarded, int64_t &swaps) {
+    IlutpShared S;
+    S.N = N;
+    S.arp = &arp;
+    S.aci = &aci;
+    S.ava = &ava;
+    S.droptol = droptol;
+    S.fill = fill;
+    S.permtol = permtol;
+    S.slot.assign(N + 1, 0);
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t cap = (int64_t)std::floor(fill * (double)(arp[i + 1] - arp[i]) / 2.0);
+        S.slot[i + 1] = S.slot[i] + std::max<int64_t>(cap, 1);
+    }
+    const int64_t total = S.slot[N];
+    S.lcnt.assign(N, 0);
+    S.ucnt.assign(N, 0);
+    S.lci.resize(total);
+    S.uci.resize(total);
+    S.lva.resize(total);
+    S.uva.resize(total);
+    S.diag.assign(N, cd(0, 0));
+    const int64_t n1 = N > 0 ? N : 1;
+    S.q.reset(new std::atomic<int32_t>[n1]);
+    S.qinv.reset(new std::atomic<int32_t>[n1]);
+    S.done.reset(new std::atomic<int>[n1]);
+    for (int64_t k = 0; k < N; ++k) {
+        S.q[k].store((int32_t)k, std::memory_order_relaxed);
+        S.qinv[k].store((int32_t)k, std::memory_order_relaxed);
+        S.done[k].store(0, std::memory_order_relaxed);
+    }
+    unsigned nt = std::max(1u, std::thread::hardware_concurrency());
+    if (const char *env = std::getenv("OMSS_ILU_THREADS")) nt = std::max(1, std::atoi(env));
+    if ((int64_t)nt > N) nt = (unsigned)std::max<int64_t>(1, N);
+    std::vector<std::thread> pool;
+    for (unsigned t = 1; t < nt; ++t) pool.emplace_back(ilutp_worker, std::ref(S));
+    ilutp_worker(S);
+    for (auto &th : pool) th.join();
+    q.resize(N);
+    std::vector<int32_t> qinv(N);
+    for (int64_t k = 0; k < N; ++k) {
+        q[k] = S.q[k].load(std::memory_order_relaxed);
+        qinv[k] = S.qinv[k].load(std::memory_order_relaxed);
+    }
+    // compact into CSR; U to positions, each row in increasing position
+    L.rp.assign(N + 1, 0);
+    U.rp.assign(N + 1, 0);
+    for (int64_t i = 0; i < N; ++i) {
+        L.rp[i + 1] = L.rp[i] + S.lcnt[i];
+        U.rp[i + 1] = U.rp[i] + S.ucnt[i];
+    }
+    L.ci.resize(L.rp[N]);
+    L.va.resize(L.rp[N]);
+    U.ci.resize(U.rp[N]);
+    U.va.resize(U.rp[N]);
+    std::vector<std::pair<int32_t, cd>> row;
+    for (int64_t i = 0; i < N; ++i) {
+        std::copy(S.lci.begin() + S.slot[i], S.lci.begin() + S.slot[i] + S.lcnt[i], L.ci.begin() + L.rp[i]);
+        std::copy(S.lva.begin() + S.slot[i], S.lva.begin() + S.slot[i] + S.lcnt[i], L.va.begin() + L.rp[i]);
+        row.clear();
+        for (int64_t e = S.slot[i]; e < S.slot[i] + S.ucnt[i]; ++e) row.push_back({qinv[S.uci[e]], S.uva[e]});
+        std::sort(row.begin(), row.end(), [](const auto &a, const auto &b) { return a.first < b.first; });
+        for (size_t t = 0; t < row.size(); ++t) {
+            U.ci[U.rp[i] + t] = row[t].first;
+            U.va[U.rp[i] + t] = row[t].second;
+        }
+    }
+    diag.swap(S.diag);
+    guarded = S.guarded.load();
+    swaps = S.swaps.load();
+}
+
 // Conjugate transpose of a strict triangular CSR.
 HostTri conj_transpose(int64_t N, const HostTri &T) {
     HostTri R;
@@ -366,16 +604,75 @@ void build_tile_plan(TilePlan &P, int64_t N, const std::vector<int64_t> &rp, con
 
 using namespace omss;
 
+namespace omss {
+namespace {
+// Equilibration of the iLUTP of Sec. II as SuperLU runs it: r_i = 1 / max_j
+// |a_ij|, then c_j = 1 / max_i |r_i a_ij|; the values become (r_i a_ij) c_j.
+// Empty rows and columns keep the scale 1.
+void equilibrate_host(int64_t N, const std::vector<int64_t> &rp, const std::vector<int32_t> &ci,
+                      std::vector<double2> &va, std::vector<double> &r, std::vector<double> &c) {
+    r.assign(N, 1.0);
+    c.assign(N, 1.0);
+    std::vector<double> cmax(N, 0.0);
+    for (int64_t i = 0; i < N; ++i) {
+        double m = 0.0;
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) m = std::max(m, std::hypot(va[e].x, va[e].y));
+        if (m > 0.0) r[i] = 1.0 / m;
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+            va[e].x *= r[i];
+            va[e].y *= r[i];
+            cmax[ci[e]] = std::max(cmax[ci[e]], std::hypot(va[e].x, va[e].y));
+        }
+    }
+    for (int64_t j = 0; j < N; ++j)
+        if (cmax[j] > 0.0) c[j] = 1.0 / cmax[j];
+    for (int64_t i = 0; i < N; ++i)
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+            va[e].x *= c[ci[e]];
+            va[e].y *= c[ci[e]];
+        }
+}
+}  // namespace
+}  // namespace omss
+
 om_ilu::~om_ilu() {
     cudaStream_t s = owner_stream;
     L.release(s);
     U.release(s);
     UH.release(s);
     LH.release(s);
+    scale_r.release(s);
+    scale_c.release(s);
+    colperm.release(s);
+    ptmp.release(s);
+    ptmp32.release(s);
 }
+
+namespace omss {
+namespace {
+om_status ilu_factor_impl(const om_matrix *A, double droptol, double fill, double permtol, int32_t flags,
+                          void *stream, om_ilu **out);
+}
+}  // namespace omss
 
 extern "C" om_status om_ilu_factor(const om_matrix *A, double droptol, double fill, int32_t flags,
                                    void *stream, om_ilu **out) {
+    return ilu_factor_impl(A, droptol, fill, 0.0, flags, stream, out);
+}
+
+extern "C" om_status om_ilutp_factor(const om_matrix *A, double droptol, double fill, double permtol,
+                                     int32_t flags, void *stream, om_ilu **out) {
+    if (!(permtol > 0.0 && permtol <= 1.0) || (flags & 1)) {
+        set_error("om_ilutp_factor: permtol must be in (0, 1] and flag 0 (compensation) is not taken");
+        return OM_EINVAL;
+    }
+    return ilu_factor_impl(A, droptol, fill, permtol, flags, stream, out);
+}
+
+namespace omss {
+namespace {
+om_status ilu_factor_impl(const om_matrix *A, double droptol, double fill, double permtol, int32_t flags,
+                          void *stream, om_ilu **out) {
     return guarded([&] {
         OM_REQUIRE(A && out, "om_ilu_factor: NULL argument");
         OM_REQUIRE(droptol >= 0 && fill > 0, "om_ilu_factor: droptol >= 0 and fill > 0 required");
@@ -388,16 +685,31 @@ extern "C" om_status om_ilu_factor(const om_matrix *A, double droptol, double fi
         const auto c0 = clk::now();
         csr_to_host(*A, rp, ci, va, s);
         const int64_t N = A->N;
+        std::vector<double> er, ec;
+        if (flags & 8) equilibrate_host(N, rp, ci, va, er, ec);
         HostTri L, U;
         std::vector<cd> diag;
         int64_t guarded_count = 0;
         const auto c1 = clk::now();
-        ilut_host(N, rp, ci, va, droptol, fill, (flags & 1) != 0, L, U, diag, guarded_count);
+        std::vector<int32_t> q;
+        int64_t swaps = 0;
+        if (permtol > 0.0)
+            ilutp_host(N, rp, ci, va, droptol, fill, permtol, L, U, diag, q, guarded_count, swaps);
+        else
+            ilut_host(N, rp, ci, va, droptol, fill, (flags & 1) != 0, L, U, diag, guarded_count);
         const auto c2 = clk::now();
         auto M = std::make_unique<om_ilu>();
         M->owner_stream = s;
         M->N = N;
         M->n_guarded = guarded_count;
+        if (permtol > 0.0) {
+            M->pivoted = true;
+            M->n_swaps = swaps;
+            M->colperm.alloc(N, s);
+            M->ptmp32.alloc(N, s);
+            if (flags & 4) M->ptmp.alloc(N, s);
+            OM_CUDA_TRY(cudaMemcpyAsync(M->colperm.p, q.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, s));
+        }
         M->nnz_l = (int64_t)L.ci.size();
         M->nnz_u = (int64_t)U.ci.size() + N;
         M->levels_l = dag_depth(N, L, true);
@@ -405,6 +717,13 @@ extern "C" om_status om_ilu_factor(const om_matrix *A, double droptol, double fi
         const auto c3 = clk::now();
         const bool want64 = (flags & 4) != 0;
         M->has_fp64 = want64;
+        if (flags & 8) {
+            M->equilibrated = true;
+            M->scale_r.alloc(N, s);
+            M->scale_c.alloc(N, s);
+            OM_CUDA_TRY(cudaMemcpyAsync(M->scale_r.p, er.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
+            OM_CUDA_TRY(cudaMemcpyAsync(M->scale_c.p, ec.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
+        }
         build_tile_plan(M->L, N, L.rp, L.ci, L.va, nullptr, true, want64, s);
         build_tile_plan(M->U, N, U.rp, U.ci, U.va, diag.data(), false, want64, s);
         if (flags & 2) {  // conjugate transposes for the adjoint sweeps
@@ -422,7 +741,28 @@ extern "C" om_status om_ilu_factor(const om_matrix *A, double droptol, double fi
         M->seconds[1] = sec(c1, c2);
         M->seconds[2] = sec(c2, c3);
         M->seconds[3] = sec(c3, c4);
+        OM_CUDA_TRY(cudaStreamSynchronize(s));  // the permutation's host copy goes out of scope
         *out = M.release();
+    });
+}
+}  // namespace
+}  // namespace omss
+
+extern "C" om_status om_ilu_pivots(const om_ilu *M, int32_t *pivoted, int64_t *n_swaps, int32_t *colperm_host,
+                                   void *stream) {
+    return guarded([&] {
+        OM_REQUIRE(M, "om_ilu_pivots: NULL handle");
+        if (pivoted) *pivoted = M->pivoted ? 1 : 0;
+        if (n_swaps) *n_swaps = M->n_swaps;
+        if (colperm_host) {
+            cudaStream_t s = as_stream(stream);
+            if (M->pivoted) {
+                OM_CUDA_TRY(cudaMemcpyAsync(colperm_host, M->colperm.p, sizeof(int32_t) * M->N, cudaMemcpyDeviceToHost, s));
+                OM_CUDA_TRY(cudaStreamSynchronize(s));
+            } else {
+                for (int64_t k = 0; k < M->N; ++k) colperm_host[k] = (int32_t)k;
+            }
+        }
     });
 }
 

@@ -59,8 +59,7 @@ struct InnerOps : KrylovOps<float2> {
         spmv_c64(A->rowptr.p, A->col.p, A->val32.p, A->N, v, out, s);
     }
     void precond(const float2 *v, float2 *out, cudaStream_t s) override {
-        tile_sweep_c64(M->L, v, out, s);
-        tile_sweep_c64(M->U, out, out, s);
+        precond_apply_c64(*M, false, v, out, s);
     }
 };
 

@@ -57,7 +57,7 @@ unsigned grid1(int64_t n) {
 
 // K (column-major n x n, zeroed before the launch), one thread per row h = c Nm + m
 __global__ void build_k(int Nc, int Nm, double om, double Delta, double kappa, double g0, double E, double Gm,
-                        double nth, double2 *K) {
+                        double nth, const double *vt, int vband, double2 *K) {
     const int n = Nc * Nm;
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= n) return;
@@ -65,7 +65,15 @@ __global__ void build_k(int Nc, int Nm, double om, double Delta, double kappa, d
     const double hd = -Delta * c + om * m;
     const double bbd = (m < Nm - 1) ? (double)(m + 1) : 0.0;  // b b^dag in the truncated space
     const double gam = kappa * c + Gm * (1.0 + nth) * m + Gm * nth * bbd;
-    K[h + (int64_t)h * n] = make_double2(-0.5 * gam, -hd);
+    K[h + (int64_t)h * n] = make_double2(-0.5 * gam, -(vband ? hd + vt[h] : hd));
+    for (int q = 1; q <= vband / 2; ++q) {  // the Sec. VI variants: m and m + 2q, same c
+        const int d = 2 * q;
+        if (m + d < Nm) {
+            const double v = vt[(int64_t)q * n + h];
+            K[h + (int64_t)(h + d) * n] = make_double2(0, -v);
+            K[(h + d) + (int64_t)h * n] = make_double2(0, -v);
+        }
+    }
     if (m + 1 < Nm) {  // g0 c sqrt(m+1) between m and m+1
         const double v = g0 * c * sqrt((double)(m + 1));
         K[h + (int64_t)(h + 1) * n] = make_double2(0, -v);
@@ -365,7 +373,7 @@ extern "C" om_status om_nojump_factor(const om_params *params, const om_build_op
         OM_REQUIRE(p.Q_m > 0.0, "om_nojump_factor: Q_m must be positive");
         const int64_t n64 = (int64_t)p.Nc * p.Nm;
         OM_REQUIRE(n64 <= 46340, "om_nojump_factor: n*n must fit in int32 rows");
-        for (double v : {p.omega_m, p.Delta, p.kappa, p.g0, p.E, p.Q_m, p.n_th})
+        for (double v : {p.omega_m, p.Delta, p.kappa, p.g0, p.E, p.Q_m, p.n_th, p.g2, p.lam})
             OM_REQUIRE(std::isfinite(v), "om_nojump_factor: non-finite parameter");
         *out = nullptr;
         cudaStream_t s = as_stream(stream);
@@ -387,9 +395,19 @@ extern "C" om_status om_nojump_factor(const om_params *params, const om_build_op
         V.alloc(nn, s);
         Vi.alloc(nn, s);
         OM_CUDA_TRY(cudaMemsetAsync(K.p, 0, sizeof(double2) * nn, s));
-        build_k<<<(n + 127) / 128, 128, 0, s>>>(p.Nc, p.Nm, p.omega_m, p.Delta, p.kappa, p.g0, p.E, Gm, nth, K.p);
+        std::vector<double> vt_host;
+        const int vband = variant_bands(p, vt_host);
+        DBuf<double> vt;
+        if (vband) {
+            vt.alloc(vt_host.size(), s);
+            OM_CUDA_TRY(cudaMemcpyAsync(vt.p, vt_host.data(), sizeof(double) * vt_host.size(),
+                                        cudaMemcpyHostToDevice, s));
+        }
+        build_k<<<(n + 127) / 128, 128, 0, s>>>(p.Nc, p.Nm, p.omega_m, p.Delta, p.kappa, p.g0, p.E, Gm, nth, vt.p,
+                                                vband, K.p);
         note_launch();
         OM_CHECK_LAUNCH();
+        vt.release(s);
         eigendecompose(n, (flags & 4) != 0, K.p, W.p, V.p, Vi.p, s);
         auto t1 = std::chrono::steady_clock::now();
         // eigenvalues: complex64 copy and the smallest divisor |lambda_i + conj(lambda_j)|

@@ -78,6 +78,20 @@ __global__ void observables_kernel(int Nc, int Nm, const double2 *rho, double *o
     }
 }
 
+// P(m) = sum_c Re rho_{(c,m),(c,m)}: the diagonal of the reduced mechanical
+// state, one thread per m, the cavity index summed in order
+__global__ void phonon_kernel(int Nc, int Nm, const double2 *rho, double *P) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= Nm) return;
+    const int64_t n = (int64_t)Nc * Nm;
+    double s = 0;
+    for (int c = 0; c < Nc; ++c) {
+        const int64_t h = (int64_t)c * Nm + m;
+        s += rho[h * (n + 1)].x;
+    }
+    P[m] = s;
+}
+
 struct ForwardOps : KrylovOps<double2> {
     const om_matrix *A;
     const om_ilu *M;
@@ -376,5 +390,29 @@ extern "C" om_status om_observables(int32_t Nc, int32_t Nm, const double *rho_de
         OM_CUDA_TRY(cudaMemcpyAsync(out, d.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
         OM_CUDA_TRY(cudaStreamSynchronize(s));
         d.release(s);
+    });
+}
+
+extern "C" om_status om_phonon_distribution(int32_t Nc, int32_t Nm, const double *rho_dev, double *P,
+                                            double moments[3], void *stream) {
+    return guarded([&] {
+        OM_REQUIRE(rho_dev && P && moments && Nc >= 1 && Nm >= 1, "om_phonon_distribution: bad argument");
+        cudaStream_t s = as_stream(stream);
+        DBuf<double> d;
+        d.alloc(Nm, s);
+        phonon_kernel<<<(Nm + 127) / 128, 128, 0, s>>>(Nc, Nm, reinterpret_cast<const double2 *>(rho_dev), d.p);
+        omss::note_launch();
+        OM_CHECK_LAUNCH();
+        OM_CUDA_TRY(cudaMemcpyAsync(P, d.p, sizeof(double) * Nm, cudaMemcpyDeviceToHost, s));
+        OM_CUDA_TRY(cudaStreamSynchronize(s));
+        d.release(s);
+        double mean = 0, second = 0;
+        for (int m = 0; m < Nm; ++m) {
+            mean += m * P[m];
+            second += (double)m * m * P[m];
+        }
+        moments[0] = mean;
+        moments[1] = second;
+        moments[2] = mean > 0 ? (second - mean * mean) / mean : 0.0;
     });
 }

@@ -257,6 +257,70 @@ __global__ void widen(const float2 *__restrict__ v, int64_t N, double2 *__restri
         out[i] = make_double2((double)v[i].x, (double)v[i].y);
 }
 
+// narrow / widen with a real scaling d (the equilibration of the factors)
+__global__ void narrow_scaled(const double *__restrict__ d, const double2 *__restrict__ v, int64_t N,
+                              float2 *__restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const double t = d[i];
+        out[i] = make_float2((float)(t * v[i].x), (float)(t * v[i].y));
+    }
+}
+__global__ void widen_scaled(const double *__restrict__ d, const float2 *__restrict__ v, int64_t N,
+                             double2 *__restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const double t = d[i];
+        out[i] = make_double2(t * (double)v[i].x, t * (double)v[i].y);
+    }
+}
+template <class T>
+__global__ void scale_vec(const double *__restrict__ d, const T *v, int64_t N, T *out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const T a = v[i];
+        const double t = d ? d[i] : 1.0;  // NULL: a copy
+        T b;
+        b.x = (decltype(a.x))(t * a.x);
+        b.y = (decltype(a.y))(t * a.y);
+        out[i] = b;
+    }
+}
+
+// out[k] = d[q[k]] in[q[k]] (gather) or out[q[k]] = d[q[k]] in[k] (scatter),
+// d = NULL meaning 1: the column permutation of pivoted factors together with
+// the equilibration scaling of that side
+template <class Tin, class Tout, bool SCATTER>
+__global__ void perm_scale(const int32_t *__restrict__ q, const double *__restrict__ d, const Tin *__restrict__ in,
+                           int64_t N, Tout *__restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += stride) {
+        const int32_t c = q[k];
+        const double t = d ? d[c] : 1.0;
+        const Tin a = in[SCATTER ? k : c];
+        Tout b;
+        b.x = (decltype(b.x))(t * (double)a.x);
+        b.y = (decltype(b.y))(t * (double)a.y);
+        out[SCATTER ? c : k] = b;
+    }
+}
+
+static unsigned vec_grid(int64_t N) {
+    int64_t need = (N + 255) / 256;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 4));
+}
+
+void scale_c128(const double *d, const double2 *v, int64_t N, double2 *out, cudaStream_t s) {
+    scale_vec<double2><<<vec_grid(N), 256, 0, s>>>(d, v, N, out);
+    omss::note_launch();
+    OM_CHECK_LAUNCH();
+}
+void scale_c64(const double *d, const float2 *v, int64_t N, float2 *out, cudaStream_t s) {
+    scale_vec<float2><<<vec_grid(N), 256, 0, s>>>(d, v, N, out);
+    omss::note_launch();
+    OM_CHECK_LAUNCH();
+}
+
 void to_c64(const double2 *v, int64_t N, float2 *out, cudaStream_t s) {
     int64_t need = (N + 255) / 256;
     unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 4));
@@ -305,16 +369,127 @@ void precond_apply(const om_ilu &M, bool conj_transpose, bool fp64, const double
     OM_REQUIRE(!conj_transpose || M.has_transpose, "factor built without conjugate transposes");
     const TilePlan &first = conj_transpose ? M.UH : M.L;
     const TilePlan &second = conj_transpose ? M.LH : M.U;
-    if (fp64) {
-        OM_REQUIRE(M.has_fp64, "factor built without complex128 sweep data");
-        tile_sweep_c128(first, v, z, s);
-        tile_sweep_c128(second, z, z, s);
+    // M^{-1} = diag(c) (L U)^{-1} diag(r); M^{-H} = diag(r) (L U)^{-H} diag(c)
+    const double *pre = M.equilibrated ? (conj_transpose ? M.scale_c.p : M.scale_r.p) : nullptr;
+    const double *post = M.equilibrated ? (conj_transpose ? M.scale_r.p : M.scale_c.p) : nullptr;
+    if (M.pivoted) {
+        // M^{-1} = diag(c) Q U^{-1} L^{-1} diag(r): the sweeps run in position
+        // space and the result is scattered; M^{-H} = diag(r) L^{-H} U^{-H}
+        // Q^T diag(c): the input is gathered
+        const unsigned g = vec_grid(M.N);
+        const int32_t *q = M.colperm.p;
+        if (fp64) {
+            OM_REQUIRE(M.has_fp64 && M.ptmp.p, "factor built without complex128 sweep data");
+            double2 *t = M.ptmp.p;
+            if (conj_transpose)
+                perm_scale<double2, double2, false><<<g, 256, 0, s>>>(q, pre, v, M.N, t);
+            else if (pre)
+                scale_vec<double2><<<g, 256, 0, s>>>(pre, v, M.N, t);
+            else
+                OM_CUDA_TRY(cudaMemcpyAsync(t, v, sizeof(double2) * M.N, cudaMemcpyDeviceToDevice, s));
+            omss::note_launch();
+            OM_CHECK_LAUNCH();
+            tile_sweep_c128(first, t, t, s);
+            tile_sweep_c128(second, t, t, s);
+            if (conj_transpose) {
+                if (post)
+                    scale_vec<double2><<<g, 256, 0, s>>>(post, t, M.N, z);
+                else
+                    OM_CUDA_TRY(cudaMemcpyAsync(z, t, sizeof(double2) * M.N, cudaMemcpyDeviceToDevice, s));
+            } else {
+                perm_scale<double2, double2, true><<<g, 256, 0, s>>>(q, post, t, M.N, z);
+            }
+            omss::note_launch();
+            OM_CHECK_LAUNCH();
+            return;
+        }
+        if (conj_transpose)
+            perm_scale<double2, float2, false><<<g, 256, 0, s>>>(q, pre, v, M.N, tmp32);
+        else if (pre)
+            narrow_scaled<<<g, 256, 0, s>>>(pre, v, M.N, tmp32);
+        else
+            narrow<<<g, 256, 0, s>>>(v, M.N, tmp32);
+        omss::note_launch();
+        OM_CHECK_LAUNCH();
+        tile_sweep_c64(first, tmp32, tmp32, s, allow_split);
+        tile_sweep_c64(second, tmp32, tmp32, s, allow_split);
+        if (conj_transpose) {
+            if (post)
+                widen_scaled<<<g, 256, 0, s>>>(post, tmp32, M.N, z);
+            else
+                widen<<<g, 256, 0, s>>>(tmp32, M.N, z);
+        } else {
+            perm_scale<float2, double2, true><<<g, 256, 0, s>>>(q, post, tmp32, M.N, z);
+        }
+        omss::note_launch();
+        OM_CHECK_LAUNCH();
         return;
     }
-    to_c64(v, M.N, tmp32, s);
+    if (fp64) {
+        OM_REQUIRE(M.has_fp64, "factor built without complex128 sweep data");
+        if (pre) {
+            scale_c128(pre, v, M.N, z, s);
+            tile_sweep_c128(first, z, z, s);
+        } else {
+            tile_sweep_c128(first, v, z, s);
+        }
+        tile_sweep_c128(second, z, z, s);
+        if (post) scale_c128(post, z, M.N, z, s);
+        return;
+    }
+    if (pre) {
+        narrow_scaled<<<vec_grid(M.N), 256, 0, s>>>(pre, v, M.N, tmp32);
+        omss::note_launch();
+        OM_CHECK_LAUNCH();
+    } else {
+        to_c64(v, M.N, tmp32, s);
+    }
     tile_sweep_c64(first, tmp32, tmp32, s, allow_split);
     tile_sweep_c64(second, tmp32, tmp32, s, allow_split);
-    to_c128(tmp32, M.N, z, s);
+    if (post) {
+        widen_scaled<<<vec_grid(M.N), 256, 0, s>>>(post, tmp32, M.N, z);
+        omss::note_launch();
+        OM_CHECK_LAUNCH();
+    } else {
+        to_c128(tmp32, M.N, z, s);
+    }
+}
+
+void precond_apply_c64(const om_ilu &M, bool conj_transpose, const float2 *v, float2 *z, cudaStream_t s,
+                       bool allow_split) {
+    OM_REQUIRE(!conj_transpose || M.has_transpose, "factor built without conjugate transposes");
+    const TilePlan &first = conj_transpose ? M.UH : M.L;
+    const TilePlan &second = conj_transpose ? M.LH : M.U;
+    const double *pre = M.equilibrated ? (conj_transpose ? M.scale_c.p : M.scale_r.p) : nullptr;
+    const double *post = M.equilibrated ? (conj_transpose ? M.scale_r.p : M.scale_c.p) : nullptr;
+    if (M.pivoted) {
+        const unsigned g = vec_grid(M.N);
+        const int32_t *q = M.colperm.p;
+        float2 *t = M.ptmp32.p;
+        if (conj_transpose)
+            perm_scale<float2, float2, false><<<g, 256, 0, s>>>(q, pre, v, M.N, t);
+        else
+            scale_vec<float2><<<g, 256, 0, s>>>(pre, v, M.N, t);
+        omss::note_launch();
+        OM_CHECK_LAUNCH();
+        tile_sweep_c64(first, t, t, s, allow_split);
+        tile_sweep_c64(second, t, t, s, allow_split);
+        if (conj_transpose)
+            scale_vec<float2><<<g, 256, 0, s>>>(post, t, M.N, z);
+        else
+            perm_scale<float2, float2, true><<<g, 256, 0, s>>>(q, post, t, M.N, z);
+        omss::note_launch();
+        OM_CHECK_LAUNCH();
+        return;
+    }
+    if (pre) {
+        scale_c64(pre, v, M.N, z, s);
+        tile_sweep_c64(first, z, z, s, allow_split);
+    } else {
+        tile_sweep_c64(first, v, z, s, allow_split);
+    }
+    tile_sweep_c64(second, z, z, s, allow_split);
+    if (post) scale_c64(post, z, M.N, z, s);
 }
 
 }  // namespace omss

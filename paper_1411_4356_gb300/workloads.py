@@ -20,6 +20,8 @@ class SystemParams:
     E: float = 0.2
     Q_m: float = 1e3
     n_th: float = 0.5
+    g2: float = 0.0   # quadratic coupling g2 (b + b^dag)^2 a^dag a (Sec. VI)
+    lam: float = 0.0  # anharmonic term lam (b + b^dag)^4 (Sec. VI)
 
     def with_(self, **kw) -> "SystemParams":
         return replace(self, **kw)
@@ -63,6 +65,14 @@ LARGE = Workload("large_20x200", SystemParams(20, 200, 1.0, -1.0, 0.5, 1.5, 0.5,
 # run on smaller systems with the 360,000-row parameters.
 ADJOINT = Workload("adjoint_12x100", SystemParams(12, 100, 1.0, -1.0, 0.5, 1.0, 0.4, 1e4, 0.5),
                    droptol=1e-4, fill=10.0, restart=30, tol=1e-10)
+# the paper's application (Sec. V, Fig. 5): the cavity-Cooper pair transistor
+# at N_c = 5, N_m = 160 (640,000 rows), n_th = 20, Delta = -2 kappa, in the
+# single-photon strong-coupling regime; Q_m is not printed for this case and
+# the 1e4 of the other systems is taken.  The thermal jumps (n_th = 20) are
+# strong against the no-jump part, so GMRES needs thousands of iterations and
+# a restart of 120 (100 stagnates); mixed precision reaches eta 1e-12.
+CCPT = Workload("ccpt_5x160", SystemParams(5, 160, 1.0, -0.1, 0.05, 0.32, 0.45, 1e4, 20.0),
+                droptol=1e-4, fill=200.0, restart=120, tol=1e-12, precision=1)
 # batched sweep base parameters (N_c = 6; Delta and N_m drawn per system).
 # ILUT(1e-5, 60): with caps of 20 and 40 some draws give an unstable factor.
 BATCH_BASE = SystemParams(6, 20, 1.0, 0.0, 0.4, 0.8, 0.2, 1e3, 0.2)
