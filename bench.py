@@ -16,7 +16,7 @@ cores.  Inputs are the system parameters; the working set (Krylov basis of
 several GB) is far larger than L2.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl omss|reference]
-                    [--workload large|mid|mid_ilu|batched]
+                    [--workload large|mid|mid_ilu|batched|sweep]
 
 For N > 1 launch with torch.distributed.run: every rank solves its own
 system (independent replicas, weak scaling).  Rank 0 prints one JSON line.
@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="headline workload only (no FP64 / 360k sub-lines)")
     ap.add_argument("--tol", type=float, default=1e-12, help="eta target of the benched solves")
-    ap.add_argument("--workload", choices=["large", "mid", "mid_ilu", "batched"], default="large",
+    ap.add_argument("--workload", choices=["large", "mid", "mid_ilu", "batched", "sweep"], default="large",
                     help="large: 16M rows, mixed precision (default); mid: 360,000 rows, FP64, no-jump "
                          "preconditioner; mid_ilu: 360,000 rows with the paper's RCM + ILUT; batched: the "
                          "parameter sweep (N_c = 6, N_m in {20, 30, 40, 60}), solve phase timed")
@@ -389,6 +389,17 @@ def run_omss(args):
                     max_abs_err_P=float(np.abs(st["P"] - np.array(ref["P"])).max()),
                     oracle_fano=ref["fano"], oracle_eta=ref["eta"])}
             del rho_cc
+            # the 512-system parameter sweep, each system through the whole no-jump path
+            from paper_1411_4356_gb300.workloads import batched_draws
+
+            sp_params = sorted(batched_draws(512), key=lambda q: -q.Nm)
+            sweep_pass(sp_params[:32], 16)  # warm-up
+            dt, infos, rhos = sweep_pass(sp_params, 16)
+            extras["sweep_512"] = {"value": len(sp_params) / dt, "unit": "solves/s", "ms_per_step": dt * 1e3,
+                                   "systems": len(sp_params), "concurrency": 16,
+                                   "precision": "complex64 GMRES(50) in FP64 refinement, TF32 no-jump products",
+                                   **sweep_summary(sp_params, infos, rhos)}
+            del rhos
             api.profile(True)
             dt, st = timed(lambda: ilu_step(MID, rho_mid, args.tol), stream)
             sp_ms, sp_n = api.profile_read(api.PROF_SPLIT)
@@ -699,11 +710,74 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def sweep_pass(params, concurrency):
+    """The 512-system parameter sweep through the whole no-jump path (assembly,
+    K and its eigendecomposition, mixed GMRES to eta 1e-12) on concurrent
+    streams: (seconds of the pass on the device clock, infos, rhos)."""
+    import torch
+
+    from paper_1411_4356_gb300 import api
+
+    stream = torch.cuda.current_stream()
+    dt, (rhos, infos) = timed(lambda: api.steady_state_sweep_nojump(params, restart=RESTART, tol=1e-12, precision=1,
+                                                                    concurrency=concurrency), stream)
+    return dt, infos, rhos
+
+
+def sweep_summary(params, infos, rhos):
+    """Statuses, iterations and the invariants of every system of a sweep."""
+    import torch
+
+    bad = [i for i, inf in enumerate(infos) if inf.status != 0]
+    tr = max(abs(complex(torch.diagonal(r).sum().item()) - 1) for r in rhos)
+    herm = max(float((r - r.conj().t()).abs().max().item()) for r in rhos)
+    its = [inf.iterations for inf in infos]
+    return {"failed": bad, "iterations_mean": float(np.mean(its)), "iterations_max": int(max(its)),
+            "eta_max": float(max(inf.eta for inf in infos)), "max_trace_minus_1": tr, "max_hermiticity": herm,
+            "rows_total": int(sum(p.N for p in params))}
+
+
+def run_sweep(args):
+    """--workload sweep: the first `systems` draws of the 512-system sweep
+    (N_c = 6, Delta ~ U[-3, 1], N_m in {20, 30, 40, 60}), each through the whole
+    no-jump path per step; K timed passes."""
+    import torch
+
+    from paper_1411_4356_gb300 import api
+    from paper_1411_4356_gb300.workloads import batched_draws
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    params = sorted(batched_draws(512)[: args.systems], key=lambda p: -p.Nm)
+    conc = args.concurrency if args.concurrency > 0 else 16
+    for _ in range(args.warmup):
+        sweep_pass(params, conc)
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = api.kernel_launches()
+    total = 0.0
+    for _ in range(args.steps):
+        dt, infos, rhos = sweep_pass(params, conc)
+        total += dt
+    launches = api.kernel_launches() - launches0
+    clk = clocks.stop()
+    line = {"metric": METRIC, "value": len(params) * args.steps / total, "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64 Krylov in FP64 refinement / TF32 no-jump products", "data": "synthetic",
+            "config": {"workload": "sweep_6xNm_nojump", "systems": len(params), "Nc": 6,
+                       "Nm": sorted({p.Nm for p in params}), "concurrency": conc, "restart": RESTART, "tol": 1e-12,
+                       "timed": "whole path per system (assembly, K + geev, GMRES, normalisation)"},
+            "sweep": sweep_summary(params, infos, rhos), "gpu_launches": int(launches), "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "batched":
         run_batched(a)
+    elif a.workload == "sweep":
+        run_sweep(a)
     else:
         run_omss(a)

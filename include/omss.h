@@ -319,6 +319,22 @@ void om_nojump_free(om_nojump *M);
 /* ---- single kernels, exposed for parity tests -------------------------------
  * y = A x (DEVICE c128 vectors of length nrows). */
 om_status om_spmv(const om_matrix *A, const double *x, double *y, void *stream);
+/* The parameter sweep on the no-jump path (Sec. IV: independent solves of
+ * different parameter sets run side by side).  For each of the `count`
+ * systems params[i] the whole path runs -- om_build_liouvillian with bopts,
+ * om_nojump_factor with factor_flags, om_steady_state_solve_nojump with
+ * sopts -- and rho_dev[i] (caller-owned DEVICE c128 n_i x n_i, column-major)
+ * receives the steady state; status[i] (HOST) is the first non-OK status of
+ * that system's calls, info[i] (HOST, may be NULL) its solve statistics.
+ * `concurrency` (1..64) host threads with their own non-blocking streams take
+ * the systems in the order given; the work is joined onto `stream` before
+ * the call returns, and each system's handles are freed when it is done.  A
+ * failing system does not stop the others.  Errors (of the call itself):
+ * OM_EINVAL, OM_ECUDA. */
+om_status om_steady_state_sweep_nojump(int32_t count, const om_params *params, const om_build_opts *bopts,
+                                       int32_t factor_flags, const om_solve_opts *sopts, double *const *rho_dev,
+                                       om_solve_info *info, om_status *status, int32_t concurrency, void *stream);
+
 /* y = L~ x for an UNPERMUTED matrix of om_build_liouvillian, computed from the
  * closed-form stencil of Eq. 3 (at most 13 terms per row, coefficients from
  * per-level tables) and the trace row of Eq. 5 instead of the stored CSR

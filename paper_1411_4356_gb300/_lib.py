@@ -47,6 +47,8 @@ SIGNATURES = {
     "om_matrix_export": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),
     "om_permute": (c_i32, [c_vp, c_vp, c_vp, ctypes.POINTER(c_vp)]),
     "om_ilu_factor": (c_i32, [c_vp, c_dbl, c_dbl, c_i32, c_vp, ctypes.POINTER(c_vp)]),
+    "om_steady_state_sweep_nojump": (c_i32, [c_i32, c_vp, ctypes.POINTER(om_build_opts), c_i32,
+                                             ctypes.POINTER(om_solve_opts), c_vp, c_vp, c_vp, c_i32, c_vp]),
     "om_ilutp_factor": (c_i32, [c_vp, c_dbl, c_dbl, c_dbl, c_i32, c_vp, ctypes.POINTER(c_vp)]),
     "om_ilu_pivots": (c_i32, [c_vp, ctypes.POINTER(c_i32), ctypes.POINTER(c_i64), c_vp, c_vp]),
     "om_ilu_info": (c_i32, [c_vp] + [ctypes.POINTER(c_i64)] * 5),

@@ -403,6 +403,35 @@ def observables(Nc: int, Nm: int, rho: torch.Tensor, stream=None):
     return out[0], out[1]
 
 
+def steady_state_sweep_nojump(params_list, restart: int = 50, max_iters: int = 5000, tol: float = 1e-12,
+                              precision: int = 0, trace_mode: str = "replace", nth_floor: float = 1e-15,
+                              eig32: bool = False, simt: bool = False, concurrency: int = 8, stream=None):
+    """The whole no-jump path for many parameter sets on concurrent streams
+    (om_steady_state_sweep_nojump).  Returns ([rho n x n CUDA tensors], [SolveInfo])."""
+    lib = _lib.load()
+    count = len(params_list)
+    P = (om_params * max(count, 1))(*[to_om_params(p) for p in params_list])
+    rhos = [torch.empty(p.n * p.n, dtype=torch.complex128, device="cuda") for p in params_list]
+    Rh = (ctypes.c_void_p * max(count, 1))(*[r.data_ptr() for r in rhos])
+    infos = (om_solve_info * max(count, 1))()
+    status = (ctypes.c_int32 * max(count, 1))()
+    o = _opts(restart, max_iters, tol, precision, 0)
+    b = om_build_opts(TRACE_MODES[trace_mode], nth_floor)
+    flags = (2 if simt else 0) | (4 if eig32 else 0)
+    check(lib.om_steady_state_sweep_nojump(count, ctypes.cast(P, ctypes.c_void_p), ctypes.byref(b), flags,
+                                           ctypes.byref(o), ctypes.cast(Rh, ctypes.c_void_p),
+                                           ctypes.cast(infos, ctypes.c_void_p), ctypes.cast(status, ctypes.c_void_p),
+                                           int(concurrency), ctypes.c_void_p(_stream(stream))),
+          "om_steady_state_sweep_nojump")
+    out_rho, out_info = [], []
+    for i, p in enumerate(params_list):
+        out_rho.append(rhos[i].view(p.n, p.n).t())
+        inf = infos[i]
+        out_info.append(SolveInfo(inf.iterations, inf.cycles, inf.eta, inf.trace_before, inf.seconds,
+                                  list(inf.residual_history[:min(inf.cycles, 64)]), int(status[i])))
+    return out_rho, out_info
+
+
 def phonon_distribution(Nc: int, Nm: int, rho: torch.Tensor, stream=None):
     """(P[m] numpy array, <N_b>, <N_b^2>, Fano factor) of a CUDA rho (Sec. V, Fig. 5)."""
     flat = rho.t().contiguous().view(-1) if rho.dim() == 2 else rho
