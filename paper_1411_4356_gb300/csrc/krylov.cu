@@ -395,10 +395,13 @@ __global__ void rsub(const T *__restrict__ b, T *y, int64_t N) {
     }
 }
 
+// y = a x + b y; with b = 0 y is written without being read, so that an
+// uninitialised y (whose bits may spell NaN) does not leak into the result
 __global__ void axpby_kernel(double2 a, const double2 *__restrict__ x, double2 b, double2 *y, int64_t N) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const bool keep_y = b.x != 0.0 || b.y != 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride)
-        y[i] = cadd(cmul(a, x[i]), cmul(b, y[i]));
+        y[i] = keep_y ? cadd(cmul(a, x[i]), cmul(b, y[i])) : cmul(a, x[i]);
 }
 
 // x += sum_{k < count} y[k] Z_k
