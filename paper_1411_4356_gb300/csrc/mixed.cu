@@ -139,6 +139,11 @@ om_status mixed_solve(const om_matrix *A, KrylovOps<float2> &ops, const int32_t 
                 }
                 if (eta <= opts->tol) break;
             }
+            if (!std::isfinite(beta)) {
+                final_status = OM_ENUMERIC;
+                set_error("om_steady_state_solve (mixed precision): non-finite residual");
+                break;
+            }
             if (!(beta > 0)) break;
             if (its >= opts->max_iters) {
                 final_status = OM_ENOCONV;
