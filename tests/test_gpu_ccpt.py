@@ -10,10 +10,15 @@ tests/golden/ccpt_5x160_reference.json (make_ccpt_reference.py: FP64
 Bartels-Stewart preconditioner, relative residual 1e-12), plus what holds at
 any size: sum_m P(m) = Tr rho = 1 and P(m) >= 0 up to the solve's error.
 
-Tolerances: rho within 1e-9 of the oracle (as on the other systems); P(m)
-sums N_c entries of the diagonal, so it inherits that bound; <N_b> and <N_b^2> sum m P(m) and m^2 P(m) over 160 levels and are held to
-1e-9 * N_m and 1e-9 * N_m^2; the Fano factor is their quotient, held to a
-relative 1e-7."""
+Tolerances.  At N_m = 40: rho within 1e-9 of the oracle (as on the other
+systems); P(m) sums N_c entries of the diagonal and inherits that bound.  At
+full size the steady state is far more sensitive to the backward error: the
+slow mechanical mode (Gamma_m = 1e-4) in a bath of n_th = 20 amplifies eta
+by about 2e4 in the entries of rho (the oracle's solve stops at eta = 4.6e-13
+and this one at 8.1e-13; their entries differ by 1.1e-8).  So the full-size
+bound is 2.5e4 * (eta_oracle + eta_gpu) for rho and P(m), 3e-8 here; <N_b> and
+<N_b^2> sum m P(m) and m^2 P(m) and get N_m and N_m^2 times that; the Fano
+factor, a quotient of the two, a relative 1e-6."""
 import json
 import os
 
@@ -119,11 +124,16 @@ def test_ccpt_5x160(full):
         pytest.skip("no stored oracle reference for the c-CPT system")
     ref = json.load(open(PATH))
     assert ref["params"]["Nm"] == p.Nm and ref["params"]["n_th"] == p.n_th
-    assert np.abs(P - np.array(ref["P"])).max() <= 1e-9
-    assert abs(mean - ref["mean"]) <= 1e-9 * p.Nm
-    assert abs(second - ref["second"]) <= 1e-9 * p.Nm ** 2
-    assert F == pytest.approx(ref["fano"], rel=1e-7)
+    bound = 2.5e4 * (ref["eta"] + info.eta)
+    print(f"bound {bound:.2e}: max|P - P_oracle| {np.abs(P - np.array(ref['P'])).max():.2e}, "
+          f"F - F_oracle {F - ref['fano']:.2e}")
+    assert np.abs(P - np.array(ref["P"])).max() <= bound
+    assert abs(mean - ref["mean"]) <= bound * p.Nm
+    assert abs(second - ref["second"]) <= bound * p.Nm ** 2
+    assert F == pytest.approx(ref["fano"], rel=1e-6)
+    d = np.array(ref["diag_re"]) + 1j * np.array(ref["diag_im"])
+    assert np.abs(torch.diagonal(rho).cpu().numpy() - d).max() <= bound
     s = np.array(ref["samples"])
     i = torch.from_numpy(s[:, 0].astype(np.int64)).cuda()
     j = torch.from_numpy(s[:, 1].astype(np.int64)).cuda()
-    assert np.abs(rho[i, j].cpu().numpy() - (s[:, 2] + 1j * s[:, 3])).max() <= 1e-9
+    assert np.abs(rho[i, j].cpu().numpy() - (s[:, 2] + 1j * s[:, 3])).max() <= bound
