@@ -712,15 +712,15 @@ def run_reference(args):
 
 def sweep_pass(params, concurrency):
     """The 512-system parameter sweep through the whole no-jump path (assembly,
-    K and its eigendecomposition, mixed GMRES to eta 1e-12) on concurrent
-    streams: (seconds of the pass on the device clock, infos, rhos)."""
+    K and its complex64 eigendecomposition, mixed GMRES to eta 1e-12) on
+    concurrent streams: (seconds of the pass on the device clock, infos, rhos)."""
     import torch
 
     from paper_1411_4356_gb300 import api
 
     stream = torch.cuda.current_stream()
     dt, (rhos, infos) = timed(lambda: api.steady_state_sweep_nojump(params, restart=RESTART, tol=1e-12, precision=1,
-                                                                    concurrency=concurrency), stream)
+                                                                    concurrency=concurrency, eig32=True), stream)
     return dt, infos, rhos
 
 
@@ -766,6 +766,7 @@ def run_sweep(args):
             "dtype": "c64 Krylov in FP64 refinement / TF32 no-jump products", "data": "synthetic",
             "config": {"workload": "sweep_6xNm_nojump", "systems": len(params), "Nc": 6,
                        "Nm": sorted({p.Nm for p in params}), "concurrency": conc, "restart": RESTART, "tol": 1e-12,
+                       "eigendecomposition": "complex64",
                        "timed": "whole path per system (assembly, K + geev, GMRES, normalisation)"},
             "sweep": sweep_summary(params, infos, rhos), "gpu_launches": int(launches), "clocks": clk}
     print(json.dumps(line), flush=True)
