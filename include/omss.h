@@ -157,6 +157,17 @@ om_status om_matrix_export(const om_matrix *A, int64_t *rowptr, int32_t *col, do
  * A_rcm[r, c] = A[perm[r], perm[c]].  Errors: OM_EINVAL on NULL arguments. */
 om_status om_permute(const om_matrix *A, void *stream, int32_t *perm_dev, om_matrix **A_rcm);
 
+/* om_permute computes the order on the device; om_permute_ex chooses: flags
+ * bit 0 set, on the device, level by level (each breadth-first level is the
+ * previous level's unplaced neighbours sorted by (position of the earliest
+ * neighbour in the previous level, degree, index), which is the serial order
+ * above) on the union pattern built on the device, with about 40 bytes of
+ * device memory per nonzero of A; bit 0 clear, the serial walk on the host
+ * cores.  Both give the same permutation.  Errors: OM_EINVAL (also, on the
+ * device, for a node of degree >= 2^20 in the union pattern), OM_ENOMEM,
+ * OM_ECUDA. */
+om_status om_permute_ex(const om_matrix *A, int32_t flags, void *stream, int32_t *perm_dev, om_matrix **A_rcm);
+
 /* ---- Sec. II: ILUT(d, p) ----------------------------------------------------
  * Row-wise incomplete LU of A (unit L, no pivoting).  In row i every entry
  * of modulus below droptol * ||row i of A||_inf is dropped (the diagonal is

@@ -46,6 +46,7 @@ SIGNATURES = {
     "om_matrix_info": (c_i32, [c_vp, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64), ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl)]),
     "om_matrix_export": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),
     "om_permute": (c_i32, [c_vp, c_vp, c_vp, ctypes.POINTER(c_vp)]),
+    "om_permute_ex": (c_i32, [c_vp, c_i32, c_vp, c_vp, ctypes.POINTER(c_vp)]),
     "om_ilu_factor": (c_i32, [c_vp, c_dbl, c_dbl, c_i32, c_vp, ctypes.POINTER(c_vp)]),
     "om_steady_state_sweep_nojump": (c_i32, [c_i32, c_vp, ctypes.POINTER(om_build_opts), c_i32,
                                              ctypes.POINTER(om_solve_opts), c_vp, c_vp, c_vp, c_i32, c_vp]),

@@ -160,12 +160,15 @@ def build_liouvillian(params: SystemParams, trace_mode: str = "replace", nth_flo
     return Matrix(out.value, params)
 
 
-def permute(A: Matrix, stream=None):
-    """Sec. III: (A_rcm, perm) with perm[new] = old as a CUDA int32 tensor."""
+def permute(A: Matrix, device_order: bool = True, stream=None):
+    """Sec. III: (A_rcm, perm) with perm[new] = old as a CUDA int32 tensor; the
+    RCM order is computed on the GPU, or with device_order=False by the serial
+    walk on the host (the same permutation; om_permute_ex)."""
     lib = _lib.load()
     perm = torch.empty(A.N, dtype=torch.int32, device="cuda")
     out = ctypes.c_void_p()
-    check(lib.om_permute(A.handle, ctypes.c_void_p(_stream(stream)), _ptr(perm), ctypes.byref(out)), "om_permute")
+    check(lib.om_permute_ex(A.handle, 1 if device_order else 0, ctypes.c_void_p(_stream(stream)), _ptr(perm),
+                            ctypes.byref(out)), "om_permute")
     return Matrix(out.value, A.params), perm
 
 

@@ -1,11 +1,11 @@
 // Sec. III: reverse Cuthill-McKee order of the structure of L~ + L~^T and
 // the symmetric permutation A_rcm = P A P^T.
 //
-// The ordering runs on the host over the pattern copied back from the device
-// (breadth-first search is a serial walk; the paper times it at under a
-// minute for 7e8 nonzeros on one CPU core).  The permutation of the matrix
-// itself (gather of rows, relabelling of columns, per-row sort) runs on the
-// device.
+// The ordering runs on the device, level by level (rcm_gpu.cu), or on request
+// on the host as the serial walk over the pattern copied back (the paper
+// times it at under a minute for 7e8 nonzeros on one CPU core); the two give
+// the same permutation.  The permutation of the matrix itself (gather of
+// rows, relabelling of columns, per-row sort) runs on the device.
 #include <algorithm>
 #include <memory>
 #include <numeric>
@@ -145,23 +145,36 @@ __global__ void permute_rows(const int32_t *perm, const int32_t *iperm, const in
 
 using namespace omss;
 
-extern "C" om_status om_permute(const om_matrix *A, void *stream, int32_t *perm_dev, om_matrix **A_rcm) {
+namespace omss {
+void rcm_order_device(const om_matrix &A, int32_t *perm_dev, cudaStream_t s);
+}
+
+extern "C" om_status om_permute_ex(const om_matrix *A, int32_t flags, void *stream, int32_t *perm_dev,
+                                   om_matrix **A_rcm) {
     return guarded([&] {
         OM_REQUIRE(A && perm_dev && A_rcm, "om_permute: NULL argument");
         OM_REQUIRE(!A->permuted, "om_permute: matrix is already permuted");
+        OM_REQUIRE((flags & ~1) == 0, "om_permute_ex: unknown flags");
         *A_rcm = nullptr;
         cudaStream_t s = as_stream(stream);
         const int64_t N = A->N;
         std::vector<int64_t> rp;
-        std::vector<int32_t> ci;
         rp.resize(N + 1);
-        ci.resize(A->nnz);
         OM_CUDA_TRY(cudaMemcpyAsync(rp.data(), A->rowptr.p, sizeof(int64_t) * (N + 1), cudaMemcpyDeviceToHost, s));
-        if (A->nnz)
-            OM_CUDA_TRY(cudaMemcpyAsync(ci.data(), A->col.p, sizeof(int32_t) * A->nnz, cudaMemcpyDeviceToHost, s));
-        OM_CUDA_TRY(cudaStreamSynchronize(s));
-        std::vector<int32_t> perm = rcm_order(N, rp, ci);
-        OM_CUDA_TRY(cudaMemcpyAsync(perm_dev, perm.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, s));
+        std::vector<int32_t> perm;
+        if (flags & 1) {  // the order on the device
+            rcm_order_device(*A, perm_dev, s);
+            perm.resize(N);
+            OM_CUDA_TRY(cudaMemcpyAsync(perm.data(), perm_dev, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, s));
+            OM_CUDA_TRY(cudaStreamSynchronize(s));
+        } else {
+            std::vector<int32_t> ci(A->nnz);
+            if (A->nnz)
+                OM_CUDA_TRY(cudaMemcpyAsync(ci.data(), A->col.p, sizeof(int32_t) * A->nnz, cudaMemcpyDeviceToHost, s));
+            OM_CUDA_TRY(cudaStreamSynchronize(s));
+            perm = rcm_order(N, rp, ci);
+            OM_CUDA_TRY(cudaMemcpyAsync(perm_dev, perm.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, s));
+        }
 
         auto B = std::make_unique<om_matrix>();
         B->owner_stream = s;
@@ -254,4 +267,8 @@ extern "C" om_status om_permute(const om_matrix *A, void *stream, int32_t *perm_
         OM_CUDA_TRY(cudaStreamSynchronize(s));
         *A_rcm = B.release();
     });
+}
+
+extern "C" om_status om_permute(const om_matrix *A, void *stream, int32_t *perm_dev, om_matrix **A_rcm) {
+    return om_permute_ex(A, 1, stream, perm_dev, A_rcm);
 }
