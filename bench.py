@@ -389,6 +389,41 @@ def run_omss(args):
                     max_abs_err_P=float(np.abs(st["P"] - np.array(ref["P"])).max()),
                     oracle_fano=ref["fano"], oracle_eta=ref["eta"])}
             del rho_cc
+            # the adjoint configuration (1.44M rows): forward solve, then the
+            # adjoint solve for d<b^dag b>/d(Delta, E, g0, kappa); a central
+            # difference in E as a check
+            from paper_1411_4356_gb300 import ADJOINT
+
+            def adjoint_step():
+                q = ADJOINT.params
+                Aa = api.build_liouvillian(q, ADJOINT.trace_mode, ADJOINT.nth_floor)
+                Ma = api.nojump_factor(q, nth_floor=ADJOINT.nth_floor, adjoint=True)
+                ra, ia = api.steady_state_solve_nojump(Aa, Ma, restart=RESTART, tol=1e-13, max_iters=600)
+                hh = torch.arange(q.n, device="cuda")
+                G = torch.diag((hh % q.Nm).to(torch.complex128))
+                g, ga = api.steady_state_adjoint_nojump(Aa, Ma, ra, G, restart=RESTART, tol=1e-11, max_iters=600)
+                out = dict(forward_iterations=ia.iterations, adjoint_iterations=ga.iterations, eta=ia.eta,
+                           gradient_n_b=dict(zip(("Delta", "E", "g0", "kappa"), [float(x) for x in g])))
+                Ma.free()
+                Aa.free()
+                return out
+
+            adjoint_step()
+            dt, st = timed(adjoint_step, stream)
+
+            def n_b_at(**kw):
+                q = ADJOINT.params.with_(**kw)
+                Aq = api.build_liouvillian(q, ADJOINT.trace_mode, ADJOINT.nth_floor)
+                Mq = api.nojump_factor(q, nth_floor=ADJOINT.nth_floor)
+                rq, _ = api.steady_state_solve_nojump(Aq, Mq, restart=RESTART, tol=1e-14, max_iters=600)
+                return api.observables(q.Nc, q.Nm, rq)[1]
+
+            hE = 1e-4
+            fdE = (n_b_at(E=ADJOINT.params.E + hE) - n_b_at(E=ADJOINT.params.E - hE)) / (2 * hE)
+            extras["adjoint_12x100"] = {
+                "value": world / dt, "unit": "gradients/s (4 parameters, one observable)", "ms_per_step": dt * 1e3,
+                **st, "fd_check": {"parameter": "E", "central_difference": fdE, "step": hE,
+                                   "rel_diff": abs(st["gradient_n_b"]["E"] - fdE) / abs(fdE)}}
             # the 512-system parameter sweep, each system through the whole no-jump path
             from paper_1411_4356_gb300.workloads import batched_draws
 
