@@ -2,8 +2,11 @@
 // restarted GMRES (Sec. IV), right-preconditioned in its flexible form.
 //
 // Per inner step j the basis is extended with classical Gram-Schmidt applied
-// twice (CGS2): h = V^H w and w -= V h, repeated once, in fused multi-dot and
-// multi-axpy kernels that stream each basis vector once per pass.  Dot
+// twice (CGS2): h = V^H w and w -= V h, repeated once.  With complex128
+// vectors the basis is streamed three times per step: the first dots, the
+// first update fused with the second dots (the chunk just streamed is read
+// again from L2), and the second update with the norm; with complex64
+// vectors four times, in kernels that keep more bytes in flight.  Dot
 // products are reduced deterministically (per-block partials summed in
 // block order by one block).  The (m+1) x m Hessenberg matrix, its Givens
 // rotations and the residual estimate |g_{j+1}| live in device memory and
@@ -15,6 +18,7 @@
 // about 1/64 of the FP32 rate, so FP64 arithmetic per element would make
 // these bandwidth-bound kernels ALU-bound.
 #include <cmath>
+#include <type_traits>
 
 #include "krylov.cuh"
 
@@ -310,6 +314,62 @@ __global__ void __launch_bounds__(kThreads) multi_axpy_rows(const T *__restrict_
     }
 }
 
+// The first CGS2 update fused with the second pass's dot products:
+// w -= sum_k h[k] V_k over the block's rows, then the block's partial sums of
+// conj(V_k) w with the updated w.  Rows go in chunks of kThreads: each thread
+// updates one row (the chunk's w staged in shared memory), then each warp
+// takes every eighth basis vector and sums over the chunk with its lanes
+// across the rows, so that a chunk's basis rows, just streamed for the
+// update, are read again from L2 and the reductions stay one per vector and
+// chunk.  FP32 accumulation within a chunk for complex64 vectors, FP64 across
+// chunks, as in multidot_rows.
+template <class T>
+__global__ void __launch_bounds__(kThreads) axpy_dot_rows(const T *__restrict__ V, int64_t N, int count,
+                                                          const double2 *__restrict__ h, T *w,
+                                                          int64_t rows_per_block, double2 *partial, int ld) {
+    using A = typename Acc<T>::A;
+    __shared__ T hs[128];
+    __shared__ T ws[kThreads];
+    __shared__ double2 acc_s[128];
+    for (int k = threadIdx.x; k < 128; k += blockDim.x) {
+        hs[k] = k < count ? narrow_to<T>(h[k]) : czero<T>();
+        acc_s[k] = make_double2(0, 0);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+    const int64_t r1 = min(N, r0 + rows_per_block);
+    for (int64_t base = r0; base < r1; base += kThreads) {
+        const int64_t i = base + threadIdx.x;
+        T wi = i < r1 ? w[i] : czero<T>();
+#pragma unroll 8
+        for (int k = 0; k < count; ++k) {
+            const T v = i < r1 ? __ldcg(V + (int64_t)k * N + i) : czero<T>();
+            const T hk = hs[k];
+            wi.x -= hk.x * v.x - hk.y * v.y;
+            wi.y -= hk.x * v.y + hk.y * v.x;
+        }
+        if (i < r1) w[i] = wi;
+        ws[threadIdx.x] = wi;  // zero past r1
+        __syncthreads();
+        const int64_t rows = min((int64_t)kThreads, r1 - base);
+        for (int k = warp; k < count; k += kThreads / 32) {
+            const T *vk = V + (int64_t)k * N + base;
+            A acc = czero<A>();
+            for (int r = lane; r < rows; r += 32) {
+                const T v = __ldcg(vk + r);
+                const T x = ws[r];
+                acc.x += v.x * x.x + v.y * x.y;
+                acc.y += v.x * x.y - v.y * x.x;
+            }
+            acc = warp_sum_acc(acc);
+            if (lane == 0) acc_s[k] = cadd(acc_s[k], make_double2((double)acc.x, (double)acc.y));
+        }
+        __syncthreads();
+    }
+    for (int k = threadIdx.x; k < count; k += blockDim.x) partial[(int64_t)blockIdx.x * ld + k] = acc_s[k];
+}
+
 // sum / max partials of |x_i|^2
 template <class T>
 __global__ void __launch_bounds__(kThreads) vec_stats(const T *__restrict__ x, int64_t N, double *part_sum,
@@ -592,24 +652,34 @@ GmresResult gmres_cycle(KrylovOps<T> &ops, const T *b, T *x, double target, int 
         // CGS2: h1 = V^H w, w -= V h1; h2 = V^H w, w -= V h2; h = h1 + h2
         {
             ProfScope prof(PROF_KRYLOV, s);
-            for (int pass = 0; pass < 2; ++pass) {
+            // pass 1: h1 = V^H w
+            multidot_rows<T><<<nb, kThreads, 0, s>>>(W.V.p, N, j + 1, W.w.p, rpb, W.partial.p, ld);
+            omss::note_launch();
+            finish_dots<<<j + 1, 32, 0, s>>>(W.partial.p, nb, j + 1, ld, W.h.p, 0);
+            omss::note_launch();
+            if (std::is_same<T, double2>::value) {
+                // complex128 (FP64-ALU-bound): w -= V h1 fused with the partials of
+                // h2 = V^H w, one stream of V
+                axpy_dot_rows<T><<<nb, kThreads, 0, s>>>(W.V.p, N, j + 1, W.h.p, W.w.p, rpb, W.partial.p, ld);
+                omss::note_launch();
+            } else {
+                // complex64 (bandwidth-bound): separate passes keep more bytes in
+                // flight per thread than the fused kernel, and measure faster
+                multi_axpy_rows<T><<<nb, kThreads, 0, s>>>(W.V.p, N, j + 1, W.h.p, W.w.p, rpb, nullptr);
+                omss::note_launch();
                 multidot_rows<T><<<nb, kThreads, 0, s>>>(W.V.p, N, j + 1, W.w.p, rpb, W.partial.p, ld);
                 omss::note_launch();
-                finish_dots<<<j + 1, 32, 0, s>>>(W.partial.p, nb, j + 1, ld, W.h.p, pass);
-                omss::note_launch();
-                if (pass == 0) {
-                    multi_axpy_rows<T><<<nb, kThreads, 0, s>>>(W.V.p, N, j + 1, W.h.p, W.w.p, rpb, nullptr);
-                    omss::note_launch();
-                } else {
-                    finish_dots<<<j + 1, 32, 0, s>>>(W.partial.p, nb, j + 1, ld, W.y2.p, 0);
-                    omss::note_launch();
-                    multi_axpy_rows<T><<<nb, kThreads, 0, s>>>(W.V.p, N, j + 1, W.y2.p, W.w.p, rpb, W.scal.p + 8);
-                    omss::note_launch();
-                    finish_norm<<<1, 32, 0, s>>>(W.scal.p + 8, nb, d_nrm);
-                    omss::note_launch();
-                }
-                OM_CHECK_LAUNCH();
             }
+            finish_dots<<<j + 1, 32, 0, s>>>(W.partial.p, nb, j + 1, ld, W.h.p, 1);
+            omss::note_launch();
+            finish_dots<<<j + 1, 32, 0, s>>>(W.partial.p, nb, j + 1, ld, W.y2.p, 0);
+            omss::note_launch();
+            // w -= V h2 and |w|^2
+            multi_axpy_rows<T><<<nb, kThreads, 0, s>>>(W.V.p, N, j + 1, W.y2.p, W.w.p, rpb, W.scal.p + 8);
+            omss::note_launch();
+            finish_norm<<<1, 32, 0, s>>>(W.scal.p + 8, nb, d_nrm);
+            omss::note_launch();
+            OM_CHECK_LAUNCH();
         }
         scale_into<T><<<grid_for(N), kThreads, 0, s>>>(W.w.p, d_nrm, N, vnext);
         omss::note_launch();
