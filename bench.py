@@ -213,7 +213,7 @@ class NojumpStep:
         M = api.nojump_factor(p, nth_floor=w.nth_floor, eig32=self.eig32)
         h2 = time.perf_counter()
         _, info = api.steady_state_solve_nojump(A, M, restart=self.restart, tol=self.tol, precision=self.precision,
-                                                rho_out=self.rho_dev, max_iters=8000)
+                                                rho_out=self.rho_dev, max_iters=12000)
         obs = api.observables(p.Nc, p.Nm, self.rho_dev)
         P, mean, second, fano = api.phonon_distribution(p.Nc, p.Nm, self.rho_dev)
         st = dict(N=A.N, nnz=A.nnz, iterations=info.iterations, cycles=info.cycles, eta=info.eta,

@@ -4,12 +4,12 @@ steady state of the cavity-Cooper pair transistor of Sec. V (Fig. 5: N_c = 5,
 N_m = 160, E = 0.45, kappa = 0.05, Delta = -2 kappa, g0 = 0.32, n_th = 20),
 computed by the oracle alone: GMRES(120) on L~ (Eq. 5) right-preconditioned
 by the FP64 Bartels-Stewart inverse of the no-jump operator
-(oracle/nojump.py), to a relative residual of 1e-12.  Run from the
+(oracle/nojump.py), to a relative residual of 1e-14.  Run from the
 repository root:
 
     python tests/golden/make_ccpt_reference.py
 
-It takes about two hours (some 3,000 iterations, each a triangular
+It takes about an hour on 8 cores (some 4,900 iterations, each a triangular
 Sylvester solve of order 800).
 """
 import json
@@ -32,8 +32,8 @@ def main():
     q = CCPT.params
     p = Params(q.Nc, q.Nm, q.omega_m, q.Delta, q.kappa, q.g0, q.E, q.Q_m, q.n_th)
     t0 = time.time()
-    x, its, ok, secs = steady_state_nojump(p, CCPT.trace_mode, CCPT.nth_floor, restart=CCPT.restart, rtol=1e-12,
-                                           max_iterations=10000)
+    x, its, ok, secs = steady_state_nojump(p, CCPT.trace_mode, CCPT.nth_floor, restart=CCPT.restart, rtol=1e-14,
+                                           max_iterations=15000)
     n = q.Nc * q.Nm
     Lt, b, w, L = augmented(p, CCPT.trace_mode, CCPT.nth_floor)
     e = eta(L, x)

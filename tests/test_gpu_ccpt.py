@@ -7,18 +7,17 @@ om_phonon_distribution is checked against the oracle's partial trace
 c-CPT parameters against the oracle's no-jump GMRES at N_m = 40, and the full
 N_c = 5, N_m = 160 solve (640,000 rows) against the stored oracle reference
 tests/golden/ccpt_5x160_reference.json (make_ccpt_reference.py: FP64
-Bartels-Stewart preconditioner, relative residual 1e-12), plus what holds at
+Bartels-Stewart preconditioner, relative residual 1e-14), plus what holds at
 any size: sum_m P(m) = Tr rho = 1 and P(m) >= 0 up to the solve's error.
 
-Tolerances.  At N_m = 40: rho within 1e-9 of the oracle (as on the other
-systems); P(m) sums N_c entries of the diagonal and inherits that bound.  At
-full size the steady state is far more sensitive to the backward error: the
-slow mechanical mode (Gamma_m = 1e-4) in a bath of n_th = 20 amplifies eta
-by about 2e4 in the entries of rho (the oracle's solve stops at eta = 4.6e-13
-and this one at 8.1e-13; their entries differ by 1.1e-8).  So the full-size
-bound is 2.5e4 * (eta_oracle + eta_gpu) for rho and P(m), 3e-8 here; <N_b> and
-<N_b^2> sum m P(m) and m^2 P(m) and get N_m and N_m^2 times that; the Fano
-factor, a quotient of the two, a relative 1e-6."""
+Tolerances: rho within 1e-9 of the oracle, at N_m = 40 and at full size; P(m)
+sums N_c entries of the diagonal and inherits that bound; <N_b> and <N_b^2>
+sum m P(m) and m^2 P(m) and are held to 1e-9 N_m and 1e-9 N_m^2; the Fano
+factor, their quotient, to a relative 1e-7.  At full size the slow mechanical
+mode (Gamma_m = 1e-4) in a bath of n_th = 20 amplifies the backward error
+about 2e4-fold in the entries of rho (at eta = 8e-13 the entries are off by
+2e-8), so both solves go further: the oracle's to eta 5e-15, this one to
+5e-14 (the workload's tolerance)."""
 import json
 import os
 
@@ -106,14 +105,14 @@ def full():
 
 
 def test_ccpt_5x160(full):
-    """The workload's form: mixed precision reaches eta 1e-12 in some 3,300
+    """The workload's form: mixed precision reaches eta 5e-14 in some 4,400
     iterations of GMRES(120).  (The FP64 iteration stagnates on this system
     between 4e-12 and 5e-10 depending on the run; the reduced system above
     covers it.)"""
     A, M = full
     p = CCPT.params
     rho, info = api.steady_state_solve_nojump(A, M, restart=CCPT.restart, tol=CCPT.tol, precision=CCPT.precision,
-                                              max_iters=8000, raise_on_noconv=False)
+                                              max_iters=12000, raise_on_noconv=False)
     print(f"status {info.status}, {info.iterations} iterations, eta {info.eta:.2e}")
     assert info.status == 0 and info.eta <= CCPT.tol
     P, mean, second, F = api.phonon_distribution(p.Nc, p.Nm, rho)
@@ -124,13 +123,12 @@ def test_ccpt_5x160(full):
         pytest.skip("no stored oracle reference for the c-CPT system")
     ref = json.load(open(PATH))
     assert ref["params"]["Nm"] == p.Nm and ref["params"]["n_th"] == p.n_th
-    bound = 2.5e4 * (ref["eta"] + info.eta)
-    print(f"bound {bound:.2e}: max|P - P_oracle| {np.abs(P - np.array(ref['P'])).max():.2e}, "
-          f"F - F_oracle {F - ref['fano']:.2e}")
+    bound = 1e-9
+    print(f"max|P - P_oracle| {np.abs(P - np.array(ref['P'])).max():.2e}, F - F_oracle {F - ref['fano']:.2e}")
     assert np.abs(P - np.array(ref["P"])).max() <= bound
     assert abs(mean - ref["mean"]) <= bound * p.Nm
     assert abs(second - ref["second"]) <= bound * p.Nm ** 2
-    assert F == pytest.approx(ref["fano"], rel=1e-6)
+    assert F == pytest.approx(ref["fano"], rel=1e-7)
     d = np.array(ref["diag_re"]) + 1j * np.array(ref["diag_im"])
     assert np.abs(torch.diagonal(rho).cpu().numpy() - d).max() <= bound
     s = np.array(ref["samples"])
