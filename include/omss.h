@@ -202,9 +202,12 @@ om_status om_ilu_factor(const om_matrix *A_rcm, double droptol, double fill, int
  * equilibration scalings of flag bit 3 outside).  permtol in (0, 1] (0.1
  * keeps the diagonal while it is at least a tenth of the largest entry, the
  * threshold SuperLU's incomplete LU uses); flags as for om_ilu_factor except
- * bit 0 (compensation), which is rejected.  The rows are factored one after
- * the other on one host core (the pivots make row i depend on every earlier
- * pivot).  Errors: OM_EINVAL, OM_ENOMEM. */
+ * bit 0 (compensation), which is rejected.  The rows are factored in parallel
+ * on the host cores as for om_ilu_factor, each row deciding its pivot once
+ * every earlier row has, so the factors are those of the serial order (the
+ * pivots lengthen the dependency chain: expect it to be slower than ILUT).
+ * The handle keeps work vectors for the permutation: applications of one
+ * pivoted handle must not overlap on the GPU.  Errors: OM_EINVAL, OM_ENOMEM. */
 om_status om_ilutp_factor(const om_matrix *A_rcm, double droptol, double fill, double permtol, int32_t flags,
                           void *stream, om_ilu **out);
 
