@@ -60,14 +60,14 @@ class Point:
 
 def run_point(base: SystemParams, Delta: float, n_th: float, droptol: float = 1e-4, fill: float = 100.0,
               restart: int = 10, max_iters: int = 1000, tol: float = 1e-13, equilibrate: bool = True,
-              permtol: float = 0.1) -> Point:
+              permtol: float = 0.1, trace_mode: str = "replace") -> Point:
     """One point of the sweep.  n_th is used as given (no floor): 0 means the
     thermal entries are absent from L~, 1e-15 puts them in."""
     from . import api
     from ._lib import STATUS, OMError
 
     p = base.with_(Delta=Delta, n_th=n_th)
-    A = api.build_liouvillian(p, "replace", nth_floor=0.0)
+    A = api.build_liouvillian(p, trace_mode, nth_floor=0.0)
     Ar, perm = api.permute(A)
     A.free()
     t0 = time.perf_counter()
@@ -117,17 +117,21 @@ def main(argv=None):
     ap.add_argument("--no-equilibrate", action="store_true", help="factor L~ without row/column scaling")
     ap.add_argument("--permtol", type=float, default=0.1, help="column pivoting threshold (0: plain ILUT)")
     ap.add_argument("--restart", type=int, default=10, help="GMRES restart (the paper's is 10)")
+    ap.add_argument("--trace-mode", default="replace", choices=["replace", "add"],
+                    help="trace row of Eq. 5: replace row 0, or add w T as printed")
     a = ap.parse_args(argv)
     base = FIG4.with_(Nc=a.Nc, Nm=a.Nm)
     pts = []
     for nth in a.nths:
         for D in a.deltas:
-            pt = run_point(base, D, nth, equilibrate=not a.no_equilibrate, permtol=a.permtol, restart=a.restart)
+            pt = run_point(base, D, nth, equilibrate=not a.no_equilibrate, permtol=a.permtol, restart=a.restart,
+                           trace_mode=a.trace_mode)
             pts.append(pt)
             print(f"n_th {nth:<6g} Delta {D:+.2f}: fill {pt.fill:6.1f} condest {pt.condest:9.2e} "
                   f"iterations {pt.iterations:5d} converged {pt.converged!s:5} eta {pt.eta:.1e} "
                   f"({pt.status}; ILUT {pt.factor_s:.1f} s, solve {pt.solve_s:.1f} s)", flush=True)
-    res = {"params": asdict(base), "equilibrated": not a.no_equilibrate, "permtol": a.permtol,
+    res = {"params": asdict(base), "trace_mode": a.trace_mode, "equilibrated": not a.no_equilibrate,
+           "permtol": a.permtol,
            "droptol": 1e-4, "fill": 100.0,
            "restart": a.restart, "max_iters": 1000,
            "tol": 1e-13, "points": [asdict(p) for p in pts], "summary": summary(pts)}
