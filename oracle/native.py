@@ -53,6 +53,8 @@ def lib():
                                       ctypes.c_int64, _I64P, _I32P, _F64P,
                                       ctypes.c_int64, _I64P, _I32P, _F64P, _I64P]
             L.oracle_ilut.restype = ctypes.c_int
+            L.oracle_ilut_total.argtypes = L.oracle_ilut.argtypes
+            L.oracle_ilut_total.restype = ctypes.c_int
             L.oracle_ilutp.argtypes = [ctypes.c_int64, _I64P, _I32P, _F64P,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_int64, _I64P, _I32P, _F64P,

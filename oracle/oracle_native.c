@@ -282,6 +282,139 @@ int oracle_ilut(int64_t n, const int64_t *ap, const int32_t *ai, const double *a
 }
 
 /* ------------------------------------------------------------------------ */
+/* ILUT(d, p) with the fill cap read as a total: NNZ(L) + NNZ(U) <= p NNZ(A) */
+/* (Sec. II), held as a running budget over the rows in elimination order.  */
+/* Row i drops as oracle_ilut does, then keeps every surviving entry while  */
+/* the entries kept so far, its own included (the diagonal apart), stay     */
+/* within floor(p * NNZ(rows 0..i of A)); beyond that it keeps the largest  */
+/* moduli that fit (ties: the smaller column).  Where the budget never      */
+/* binds, the factors are plain threshold ILU(d).  The caller provides      */
+/* capacity floor(p NNZ(A)) + n for each factor.  Same return codes.        */
+/* ------------------------------------------------------------------------ */
+
+int oracle_ilut_total(int64_t n, const int64_t *ap, const int32_t *ai, const double *ax_,
+                      double droptol, double fill,
+                      int64_t cap_l, int64_t *lp, int32_t *li, double *lx_,
+                      int64_t cap_u, int64_t *up, int32_t *ui, double *ux_,
+                      int64_t *n_guarded) {
+    const cplx *ax = (const cplx *)ax_;
+    cplx *lx = (cplx *)lx_;
+    cplx *ux = (cplx *)ux_;
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    cplx *w = (cplx *)calloc(nn, sizeof(cplx));
+    unsigned char *present = (unsigned char *)calloc(nn, 1);
+    int32_t *cols = (int32_t *)malloc(sizeof(int32_t) * nn); /* columns present in w */
+    int32_t *heap = (int32_t *)malloc(sizeof(int32_t) * nn);
+    keep_t *cand = (keep_t *)malloc(sizeof(keep_t) * nn);
+    int32_t *sel = (int32_t *)malloc(sizeof(int32_t) * nn);
+    if (!w || !present || !cols || !heap || !cand || !sel) {
+        free(w); free(present); free(cols); free(heap); free(cand); free(sel);
+        return -1;
+    }
+    *n_guarded = 0;
+    lp[0] = 0;
+    up[0] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t nnz_i = ap[i + 1] - ap[i];
+        double row_inf = 0.0;
+        for (int64_t e = ap[i]; e < ap[i + 1]; ++e) {
+            double m = cabs(ax[e]);
+            if (m > row_inf) row_inf = m;
+        }
+        double tau = droptol * row_inf;
+        int64_t keep_cap = (int64_t)floor(fill * (double)nnz_i / 2.0);
+        if (keep_cap < 1) keep_cap = 1;
+
+        /* w := row i of A */
+        int64_t ncols = 0, hlen = 0;
+        for (int64_t e = ap[i]; e < ap[i + 1]; ++e) {
+            int32_t j = ai[e];
+            w[j] = ax[e];
+            present[j] = 1;
+            cols[ncols++] = j;
+            if (j < i) heap_push(heap, &hlen, j);
+        }
+        if (!present[i]) { /* structural zero diagonal: make room for it */
+            w[i] = 0.0;
+            present[i] = 1;
+            cols[ncols++] = (int32_t)i;
+        }
+
+        /* eliminate with the rows k < i, in increasing k */
+        while (hlen > 0) {
+            int32_t k = heap_pop(heap, &hlen);
+            cplx wk = w[k] / ux[up[k]]; /* U row k: diagonal first */
+            if (cabs(wk) < tau) {
+                w[k] = 0.0; /* dropped: no elimination with row k */
+                continue;
+            }
+            w[k] = wk;
+            for (int64_t e = up[k] + 1; e < up[k + 1]; ++e) {
+                int32_t j = ui[e];
+                if (!present[j]) {
+                    present[j] = 1;
+                    w[j] = 0.0;
+                    cols[ncols++] = j;
+                    if (j < i) heap_push(heap, &hlen, j);
+                }
+                w[j] -= wk * ux[e];
+            }
+        }
+
+        /* drop small entries; then, if the running budget is exceeded, keep the
+           largest ones of the row (L and U parts together, the diagonal apart) */
+        int64_t nc = 0;
+        for (int64_t t = 0; t < ncols; ++t) {
+            int32_t j = cols[t];
+            if (j == i) continue;
+            double m = cabs(w[j]);
+            if (w[j] != 0.0 && !(m < tau)) { cand[nc].col = j; cand[nc].mag = m; ++nc; }
+        }
+        int64_t budget = (int64_t)floor(fill * (double)ap[i + 1]) - (lp[i] + up[i]) - 1; /* off-diagonals */
+        if (budget < 0) budget = 0;
+        if (nc > budget) {
+            qsort(cand, (size_t)nc, sizeof(keep_t), cmp_keep);
+            nc = budget;
+        }
+        int64_t nl = 0, nu = 0;
+        for (int64_t t = 0; t < nc; ++t) sel[t] = cand[t].col;
+        qsort(sel, (size_t)nc, sizeof(int32_t), cmp_i32);
+        for (int64_t t = 0; t < nc; ++t) {
+            if (sel[t] < i) ++nl;
+            else ++nu;
+        }
+        if (lp[i] + nl > cap_l) return -2;
+        for (int64_t t = 0; t < nl; ++t) {
+            li[lp[i] + t] = sel[t];
+            lx[lp[i] + t] = w[sel[t]];
+        }
+        lp[i + 1] = lp[i] + nl;
+        if (up[i] + 1 + nu > cap_u) return -2;
+        cplx piv = w[i];
+        double guard = 1e-14 * row_inf;
+        if (cabs(piv) < guard || piv == 0.0) {
+            piv = guard > 0.0 ? guard : 1e-300;
+            ++*n_guarded;
+        }
+        ui[up[i]] = (int32_t)i;
+        ux[up[i]] = piv;
+        for (int64_t t = 0; t < nu; ++t) {
+            ui[up[i] + 1 + t] = sel[nl + t];
+            ux[up[i] + 1 + t] = w[sel[nl + t]];
+        }
+        up[i + 1] = up[i] + 1 + nu;
+
+        /* clear the work row */
+        for (int64_t t = 0; t < ncols; ++t) {
+            w[cols[t]] = 0.0;
+            present[cols[t]] = 0;
+        }
+    }
+    free(w); free(present); free(cols); free(heap); free(cand); free(sel);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* ILUTP: ILUT with threshold column pivoting, the "P" of the iLUTP of      */
 /* Sec. II.  Row i is eliminated as in oracle_ilut, but in the order of the */
 /* current column positions: q[k] is the column at position k, qinv its     */

@@ -132,9 +132,14 @@ class ILUFactors:
         return x
 
 
-def ilut(A: sp.csr_matrix, droptol: float, fill: float) -> ILUFactors:
+def ilut(A: sp.csr_matrix, droptol: float, fill: float, cap: str = "row") -> ILUFactors:
     """ILUT(d, p) of A (rows sorted by column); see oracle_native.c for the
-    dropping rules read from Sec. II and Sec. IV."""
+    dropping rules read from Sec. II and Sec. IV.  cap="row": at most
+    floor(p nnz_i / 2) entries in each of the L and U parts of row i;
+    cap="total": NNZ(L) + NNZ(U) <= p NNZ(A) as a running budget over the rows
+    (oracle_ilut_total)."""
+    if cap not in ("row", "total"):
+        raise ValueError(cap)
     A = sp.csr_matrix(A)
     A.sort_indices()
     n = A.shape[0]
@@ -142,20 +147,24 @@ def ilut(A: sp.csr_matrix, droptol: float, fill: float) -> ILUFactors:
     ai = np.ascontiguousarray(A.indices, dtype=np.int32)
     ax = np.ascontiguousarray(A.data, dtype=np.complex128)
     nnz_row = np.diff(ap)
-    cap_row = np.maximum(np.floor(fill * nnz_row / 2.0).astype(np.int64), 1)
-    cap = int(cap_row.sum()) + n
+    if cap == "row":
+        cap_row = np.maximum(np.floor(fill * nnz_row / 2.0).astype(np.int64), 1)
+        size = int(cap_row.sum()) + n
+    else:
+        size = int(np.floor(fill * float(ap[-1]))) + n
     lp = np.zeros(n + 1, dtype=np.int64)
     up = np.zeros(n + 1, dtype=np.int64)
-    li = np.zeros(cap, dtype=np.int32)
-    ui = np.zeros(cap, dtype=np.int32)
-    lx = np.zeros(cap, dtype=np.complex128)
-    ux = np.zeros(cap, dtype=np.complex128)
+    li = np.zeros(size, dtype=np.int32)
+    ui = np.zeros(size, dtype=np.int32)
+    lx = np.zeros(size, dtype=np.complex128)
+    ux = np.zeros(size, dtype=np.complex128)
     ng = np.zeros(1, dtype=np.int64)
-    rc = native.lib().oracle_ilut(
+    fn = native.lib().oracle_ilut if cap == "row" else native.lib().oracle_ilut_total
+    rc = fn(
         n, native.ptr(ap, _I64P), native.ptr(ai, _I32P), ax.view(np.float64).ctypes.data_as(_F64P),
         float(droptol), float(fill),
-        cap, native.ptr(lp, _I64P), native.ptr(li, _I32P), lx.view(np.float64).ctypes.data_as(_F64P),
-        cap, native.ptr(up, _I64P), native.ptr(ui, _I32P), ux.view(np.float64).ctypes.data_as(_F64P),
+        size, native.ptr(lp, _I64P), native.ptr(li, _I32P), lx.view(np.float64).ctypes.data_as(_F64P),
+        size, native.ptr(up, _I64P), native.ptr(ui, _I32P), ux.view(np.float64).ctypes.data_as(_F64P),
         native.ptr(ng, _I64P))
     if rc != 0:
         raise RuntimeError(f"oracle_ilut failed ({rc})")

@@ -240,3 +240,44 @@ def test_ilutp_complete_factorisation_pivots_by_rows_of_u(seed):
     v = rng.standard_normal(n) + 1j * rng.standard_normal(n)
     np.testing.assert_allclose(F.solve(v), np.linalg.solve(Ad, v), rtol=1e-9)
     np.testing.assert_allclose(F.solve_h(v), np.linalg.solve(Ad.conj().T, v), rtol=1e-9)
+
+
+# ---- the fill cap read as a total, NNZ(L) + NNZ(U) <= p NNZ(A), held as a running budget
+
+def test_total_budget_hand_worked():
+    """A = [[2, 0, 0], [1, 2, 0], [3, 1, 2]], d = 0, p = 0.8 (cumulative NNZ 1, 3, 6).
+    Row 0 keeps its diagonal (budget floor(0.8) - 0 - 1 < 0).  Row 1: budget
+    floor(2.4) - 1 - 1 = 0, so l10 = 0.5 goes.  Row 2: budget floor(4.8) - 2 - 1 = 1;
+    its candidates are l20 = 3/2 and l21 = 1/2, and the larger stays."""
+    A = sp.csr_matrix(np.array([[2, 0, 0], [1, 2, 0], [3, 1, 2]], dtype=complex))
+    F = ilut(A, 0.0, 0.8, cap="total")
+    np.testing.assert_array_equal(F.lp, [0, 0, 0, 1])
+    np.testing.assert_array_equal(F.li, [0])
+    np.testing.assert_allclose(F.lx, [1.5], rtol=0, atol=0)
+    np.testing.assert_allclose(np.diag(F.U().toarray()), [2, 2, 2], rtol=0, atol=0)
+    assert F.nnz_l + F.nnz_u <= 0.8 * A.nnz + 3
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_total_budget_that_never_binds_is_threshold_ilu(seed):
+    """With a budget above the natural fill, cap="total" keeps every entry that
+    survives the drop rule: the same factors as a per-row cap that never binds."""
+    rng = np.random.default_rng(seed)
+    A = diag_dominant(rng, 80, 0.06)
+    A = sp.csr_matrix(A + sp.random(80, 80, density=0.03, random_state=seed) * 5.0)
+    A.sort_indices()
+    for d in (0.0, 1e-2):
+        F, G = ilut(A, d, 200.0), ilut(A, d, 200.0, cap="total")
+        assert F.nnz_l + F.nnz_u < 200.0 * A.nnz / 4
+        for a, b in ((F.lp, G.lp), (F.li, G.li), (F.up, G.up), (F.ui, G.ui)):
+            np.testing.assert_array_equal(a, b)
+        np.testing.assert_array_equal(F.lx, G.lx)
+        np.testing.assert_array_equal(F.ux, G.ux)
+
+
+def test_total_budget_bounds_the_fill():
+    rng = np.random.default_rng(7)
+    A = diag_dominant(rng, 120, 0.05)
+    for p in (1.0, 1.5, 3.0):
+        F = ilut(A, 0.0, p, cap="total")
+        assert F.nnz_l + F.nnz_u <= np.floor(p * A.nnz) + 0  # diagonal included in the count
