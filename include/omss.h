@@ -182,7 +182,13 @@ om_status om_permute_ex(const om_matrix *A, int32_t flags, void *stream, int32_t
  * Sec. II does when SuperLU runs it -- r_i = 1 / max_j |a_ij|, then
  * c_j = 1 / max_i |r_i a_ij| -- and factor diag(r) A diag(c) (the drop rule
  * then reads the scaled rows); every application of the handle is
- * M^{-1} = diag(c) (L U)^{-1} diag(r) (M^{-H} = diag(r) (L U)^{-H} diag(c)).
+ * M^{-1} = diag(c) (L U)^{-1} diag(r) (M^{-H} = diag(r) (L U)^{-H} diag(c));
+ * bit 4: read the fill cap as a total, NNZ(L) + NNZ(U) <= fill * NNZ(A),
+ * held as a running budget over the rows in order -- row i keeps every entry
+ * that survives the drop rule while the entries kept by rows 0..i (diagonals
+ * apart from row i's own) stay within floor(fill * NNZ(rows 0..i of A)), and
+ * beyond that the largest moduli that fit (ties to the smaller column); where
+ * the budget never binds this is threshold ILU(droptol).  Not with bit 0.
  * Rows are factored in parallel on the
  * host cores (OMSS_ILU_THREADS caps the thread count); the factors are
  * identical to those of the serial row order.  On the device the factors are

@@ -173,16 +173,21 @@ def permute(A: Matrix, device_order: bool = True, stream=None):
 
 
 def ilu_factor(A: Matrix, droptol: float, fill: float, compensate: bool = False, adjoint: bool = False,
-               fp64_sweeps: bool = False, equilibrate: bool = False, permtol: float = 0.0, stream=None) -> ILU:
+               fp64_sweeps: bool = False, equilibrate: bool = False, permtol: float = 0.0, cap: str = "row",
+               stream=None) -> ILU:
     """Sec. II: ILUT(droptol, fill) of a permuted matrix; adjoint=True also keeps
     the conjugate-transposed factors for the adjoint sweeps, fp64_sweeps=True
     the complex128 sweep data, equilibrate=True factors diag(r) A diag(c)
     (row, then column equilibration), permtol > 0 adds threshold column
-    pivoting (ILUTP, om_ilutp_factor)."""
+    pivoting (ILUTP, om_ilutp_factor); cap="total" reads the fill cap as a
+    running total NNZ(L) + NNZ(U) <= fill * NNZ(A) (flag 16) instead of a cap
+    per row."""
+    if cap not in ("row", "total"):
+        raise ValueError(cap)
     lib = _lib.load()
     out = ctypes.c_void_p()
     flags = ((1 if compensate else 0) | (2 if adjoint else 0) | (4 if fp64_sweeps else 0)
-             | (8 if equilibrate else 0))
+             | (8 if equilibrate else 0) | (16 if cap == "total" else 0))
     if permtol != 0:
         check(lib.om_ilutp_factor(A.handle, float(droptol), float(fill), float(permtol), flags,
                                   ctypes.c_void_p(_stream(stream)), ctypes.byref(out)), "om_ilutp_factor")

@@ -325,6 +325,160 @@ void ilut_host(int64_t N, const std::vector<int64_t> &arp, const std::vector<int
     guarded = S.guarded.load();
 }
 
+// ILUT with the fill cap read as a total, NNZ(L) + NNZ(U) <= p NNZ(A), held
+// as a running budget over the rows in elimination order: row i drops as
+// ILUT does, then keeps every surviving entry while the entries kept so far,
+// its own included (the diagonal apart), stay within floor(p NNZ(rows 0..i
+// of A)); beyond that the largest moduli that fit win (ties: the smaller
+// column).  Where the budget never binds the factor is threshold ILU(d).
+// Rows run in parallel as in ILUT and eliminate as soon as the rows they need
+// are published; a row takes its budget once row i - 1 is done, so rows
+// finish in order.  Rows are stored in their own vectors (their sizes are
+// not known in advance).
+struct IlutTotalShared {
+    int64_t N;
+    const std::vector<int64_t> *arp;
+    const std::vector<int32_t> *aci;
+    const std::vector<double2> *ava;
+    double droptol, fill;
+    std::vector<std::vector<int32_t>> lcol, ucol;
+    std::vector<std::vector<cd>> lval, uval;
+    std::vector<cd> diag;
+    std::vector<int64_t> used;  // entries kept by rows 0 .. i-1, diagonals included
+    std::unique_ptr<std::atomic<int>[]> done;
+    std::atomic<int64_t> next{0};
+    std::atomic<int64_t> guarded{0};
+};
+
+void ilut_total_worker(IlutTotalShared &S) {
+    const int64_t N = S.N;
+    const auto &arp = *S.arp;
+    const auto &aci = *S.aci;
+    const auto &ava = *S.ava;
+    std::vector<cd> w(N, cd(0, 0));
+    double *wd = reinterpret_cast<double *>(w.data());
+    std::vector<Picked> cand, band;
+    std::vector<int32_t> chosen;
+    std::vector<double> keys;
+    for (;;) {
+        const int64_t i = S.next.fetch_add(1, std::memory_order_relaxed);
+        if (i >= N) break;
+        double anorm = 0;
+        for (int64_t e = arp[i]; e < arp[i + 1]; ++e) anorm = std::max(anorm, std::abs(cd(ava[e].x, ava[e].y)));
+        const double tau = S.droptol * anorm;
+        int64_t span_lo = i, span_hi = i;
+        if (arp[i + 1] > arp[i]) {
+            span_lo = std::min<int64_t>(span_lo, aci[arp[i]]);
+            span_hi = std::max<int64_t>(span_hi, aci[arp[i + 1] - 1]);
+        }
+        for (int64_t e = arp[i]; e < arp[i + 1]; ++e) w[aci[e]] = cd(ava[e].x, ava[e].y);
+        for (int64_t k = span_lo; k < i; ++k) {
+            if (w[k] == cd(0, 0)) continue;
+            for (int spins = 0; !S.done[k].load(std::memory_order_acquire); ++spins)
+                if (spins > 64) std::this_thread::yield();
+            const cd m = w[k] / S.diag[k];
+            if (std::abs(m) < tau) {
+                w[k] = 0;
+                continue;
+            }
+            w[k] = m;
+            const auto &uc = S.ucol[k];
+            if (uc.empty()) continue;
+            span_hi = std::max<int64_t>(span_hi, uc.back());
+            merge_row(wd, uc.data(), reinterpret_cast<const double *>(S.uval[k].data()), (int64_t)uc.size(),
+                      m.real(), m.imag());
+        }
+        // candidates in column order, by the drop rule (squared modulus as key,
+        // the exact modulus where the key cannot decide)
+        cand.clear();
+        const double t2 = tau * tau;
+        for (int64_t c = span_lo; c <= span_hi; ++c) {
+            if (c == i || w[c] == cd(0, 0)) continue;
+            const double re = w[c].real(), im = w[c].imag();
+            const double m2 = re * re + im * im;
+            bool keep;
+            if (m2 > t2 * (1 + kKeyEps)) keep = true;
+            else if (m2 < t2 * (1 - kKeyEps)) keep = false;
+            else keep = !(std::abs(w[c]) < tau);
+            if (keep) cand.push_back({(int32_t)c, m2});
+        }
+        if (i > 0)
+            for (int spins = 0; !S.done[i - 1].load(std::memory_order_acquire); ++spins)
+                if (spins > 64) std::this_thread::yield();
+        int64_t budget = (int64_t)std::floor(S.fill * (double)arp[i + 1]) - S.used[i] - 1;
+        if (budget < 0) budget = 0;
+        select_top(cand, budget, w, band, chosen, keys);
+        auto &lc = S.lcol[i];
+        auto &lv = S.lval[i];
+        auto &uc = S.ucol[i];
+        auto &uv = S.uval[i];
+        for (const Picked &p : cand) {
+            if (p.c < i) {
+                lc.push_back(p.c);
+                lv.push_back(w[p.c]);
+            } else {
+                uc.push_back(p.c);
+                uv.push_back(w[p.c]);
+            }
+        }
+        cd piv = w[i];
+        const double floor_ = 1e-14 * anorm;
+        if (std::abs(piv) < floor_ || piv == cd(0, 0)) {
+            piv = cd(floor_ > 0 ? floor_ : 1e-300, 0);
+            S.guarded.fetch_add(1, std::memory_order_relaxed);
+        }
+        S.diag[i] = piv;
+        S.used[i + 1] = S.used[i] + (int64_t)cand.size() + 1;
+        S.done[i].store(1, std::memory_order_release);
+        std::fill(w.begin() + span_lo, w.begin() + span_hi + 1, cd(0, 0));
+    }
+}
+
+void ilut_total_host(int64_t N, const std::vector<int64_t> &arp, const std::vector<int32_t> &aci,
+                     const std::vector<double2> &ava, double droptol, double fill, HostTri &L, HostTri &U,
+                     std::vector<cd> &diag, int64_t &guarded) {
+    IlutTotalShared S;
+    S.N = N;
+    S.arp = &arp;
+    S.aci = &aci;
+    S.ava = &ava;
+    S.droptol = droptol;
+    S.fill = fill;
+    S.lcol.resize(N);
+    S.ucol.resize(N);
+    S.lval.resize(N);
+    S.uval.resize(N);
+    S.diag.assign(N, cd(0, 0));
+    S.used.assign(N + 1, 0);
+    S.done.reset(new std::atomic<int>[N > 0 ? N : 1]);
+    for (int64_t i = 0; i < N; ++i) S.done[i].store(0, std::memory_order_relaxed);
+    unsigned nt = std::max(1u, std::thread::hardware_concurrency());
+    if (const char *env = std::getenv("OMSS_ILU_THREADS")) nt = std::max(1, std::atoi(env));
+    if ((int64_t)nt > N) nt = (unsigned)std::max<int64_t>(1, N);
+    std::vector<std::thread> pool;
+    for (unsigned t = 1; t < nt; ++t) pool.emplace_back(ilut_total_worker, std::ref(S));
+    ilut_total_worker(S);
+    for (auto &th : pool) th.join();
+    L.rp.assign(N + 1, 0);
+    U.rp.assign(N + 1, 0);
+    for (int64_t i = 0; i < N; ++i) {
+        L.rp[i + 1] = L.rp[i] + (int64_t)S.lcol[i].size();
+        U.rp[i + 1] = U.rp[i] + (int64_t)S.ucol[i].size();
+    }
+    L.ci.resize(L.rp[N]);
+    L.va.resize(L.rp[N]);
+    U.ci.resize(U.rp[N]);
+    U.va.resize(U.rp[N]);
+    for (int64_t i = 0; i < N; ++i) {
+        std::copy(S.lcol[i].begin(), S.lcol[i].end(), L.ci.begin() + L.rp[i]);
+        std::copy(S.lval[i].begin(), S.lval[i].end(), L.va.begin() + L.rp[i]);
+        std::copy(S.ucol[i].begin(), S.ucol[i].end(), U.ci.begin() + U.rp[i]);
+        std::copy(S.uval[i].begin(), S.uval[i].end(), U.va.begin() + U.rp[i]);
+    }
+    diag.swap(S.diag);
+    guarded = S.guarded.load();
+}
+
 // ILUTP: ILUT with threshold column pivoting (the "P" of the iLUTP of
 // Sec. II).  Row i eliminates, in increasing position, the columns at
 // positions below i (q[k]: the column at position k, qinv its inverse), with
@@ -676,6 +830,8 @@ om_status ilu_factor_impl(const om_matrix *A, double droptol, double fill, doubl
     return guarded([&] {
         OM_REQUIRE(A && out, "om_ilu_factor: NULL argument");
         OM_REQUIRE(droptol >= 0 && fill > 0, "om_ilu_factor: droptol >= 0 and fill > 0 required");
+        OM_REQUIRE(!((flags & 16) && ((flags & 1) || permtol > 0.0)),
+                   "om_ilu_factor: the total fill budget (flag 16) takes neither compensation nor pivoting");
         *out = nullptr;
         cudaStream_t s = as_stream(stream);
         std::vector<int64_t> rp;
@@ -695,6 +851,8 @@ om_status ilu_factor_impl(const om_matrix *A, double droptol, double fill, doubl
         int64_t swaps = 0;
         if (permtol > 0.0)
             ilutp_host(N, rp, ci, va, droptol, fill, permtol, L, U, diag, q, guarded_count, swaps);
+        else if (flags & 16)
+            ilut_total_host(N, rp, ci, va, droptol, fill, L, U, diag, guarded_count);
         else
             ilut_host(N, rp, ci, va, droptol, fill, (flags & 1) != 0, L, U, diag, guarded_count);
         const auto c2 = clk::now();

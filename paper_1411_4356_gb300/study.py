@@ -60,7 +60,7 @@ class Point:
 
 def run_point(base: SystemParams, Delta: float, n_th: float, droptol: float = 1e-4, fill: float = 100.0,
               restart: int = 10, max_iters: int = 1000, tol: float = 1e-13, equilibrate: bool = True,
-              permtol: float = 0.1, trace_mode: str = "replace") -> Point:
+              permtol: float = 0.1, trace_mode: str = "replace", cap: str = "row") -> Point:
     """One point of the sweep.  n_th is used as given (no floor): 0 means the
     thermal entries are absent from L~, 1e-15 puts them in."""
     from . import api
@@ -71,7 +71,7 @@ def run_point(base: SystemParams, Delta: float, n_th: float, droptol: float = 1e
     Ar, perm = api.permute(A)
     A.free()
     t0 = time.perf_counter()
-    M = api.ilu_factor(Ar, droptol, fill, equilibrate=equilibrate, permtol=permtol, fp64_sweeps=True)
+    M = api.ilu_factor(Ar, droptol, fill, equilibrate=equilibrate, permtol=permtol, fp64_sweeps=True, cap=cap)
     t1 = time.perf_counter()
     ce = api.ilu_condest(M, fp64=True)
     status, its, eta, ok = "OM_OK", max_iters, math.inf, False
@@ -119,18 +119,20 @@ def main(argv=None):
     ap.add_argument("--restart", type=int, default=10, help="GMRES restart (the paper's is 10)")
     ap.add_argument("--trace-mode", default="replace", choices=["replace", "add"],
                     help="trace row of Eq. 5: replace row 0, or add w T as printed")
+    ap.add_argument("--cap", default="row", choices=["row", "total"],
+                    help="fill cap p per row (floor(p nnz_i / 2) in L and in U) or as a running total")
     a = ap.parse_args(argv)
     base = FIG4.with_(Nc=a.Nc, Nm=a.Nm)
     pts = []
     for nth in a.nths:
         for D in a.deltas:
             pt = run_point(base, D, nth, equilibrate=not a.no_equilibrate, permtol=a.permtol, restart=a.restart,
-                           trace_mode=a.trace_mode)
+                           trace_mode=a.trace_mode, cap=a.cap)
             pts.append(pt)
             print(f"n_th {nth:<6g} Delta {D:+.2f}: fill {pt.fill:6.1f} condest {pt.condest:9.2e} "
                   f"iterations {pt.iterations:5d} converged {pt.converged!s:5} eta {pt.eta:.1e} "
                   f"({pt.status}; ILUT {pt.factor_s:.1f} s, solve {pt.solve_s:.1f} s)", flush=True)
-    res = {"params": asdict(base), "trace_mode": a.trace_mode, "equilibrated": not a.no_equilibrate,
+    res = {"params": asdict(base), "trace_mode": a.trace_mode, "cap": a.cap, "equilibrated": not a.no_equilibrate,
            "permtol": a.permtol,
            "droptol": 1e-4, "fill": 100.0,
            "restart": a.restart, "max_iters": 1000,
