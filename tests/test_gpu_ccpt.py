@@ -96,6 +96,22 @@ def test_reduced_ccpt_matches_oracle(precision):
     assert F == pytest.approx(fano_factor(Pr), rel=1e-7)
 
 
+def test_reduced_ccpt_paper_path():
+    """Fig. 5's own method at N_m = 40: RCM, ILUT(1e-4, 200) with the fill cap
+    read as a total (NNZ(L) + NNZ(U) <= 200 NNZ(A); the per-row reading leaves
+    an unstable factor on this system), GMRES(10); against the oracle's
+    no-jump GMRES."""
+    p = ccpt(40)
+    A = api.build_liouvillian(p)
+    Ar, perm = api.permute(A)
+    M = api.ilu_factor(Ar, 1e-4, 200.0, cap="total")
+    rho, info = api.steady_state_solve(Ar, M, perm, restart=10, tol=1e-13, max_iters=1000)
+    x, its, ok, _ = steady_state_nojump(oparams(p), restart=CCPT.restart, rtol=1e-14)
+    print(f"paper path at 5x40: fill {M.fill:.1f}, {info.iterations} iterations, eta {info.eta:.1e}")
+    assert ok and info.eta <= 1e-13
+    assert np.abs(rho.cpu().numpy() - x.reshape((p.n, p.n), order="F")).max() <= 1e-9
+
+
 @pytest.fixture(scope="module")
 def full():
     p = CCPT.params
