@@ -26,3 +26,14 @@ def test_summary_groups_by_temperature():
     assert s["3.0"]["converged"] == 3 and s["3.0"]["iterations_converged"] == [12, 14, 16]
     assert s["3.0"]["condest_median"] == 2e5 and s["3.0"]["condest_max"] == 3e5
     assert s["3.0"]["fill_mean"] == 32.0
+
+
+def test_ccpt_workload_is_fig5():
+    """Fig. 5: E = 0.45, kappa = 0.05, Delta = -2 kappa, g0 = 0.32, n_th = 20 (units of
+    omega_m), N_c = 5, N_m = 160."""
+    from paper_1411_4356_gb300 import CCPT
+
+    p = CCPT.params
+    assert (p.Nc, p.Nm) == (5, 160) and p.n == 800 and p.N == 640000
+    assert p.E == 0.45 and p.kappa == 0.05 and p.Delta == -2 * p.kappa and p.g0 == 0.32 and p.n_th == 20.0
+    assert p.g2 == 0.0 and p.lam == 0.0
