@@ -217,6 +217,27 @@ om_status om_ilu_factor(const om_matrix *A_rcm, double droptol, double fill, int
 om_status om_ilutp_factor(const om_matrix *A_rcm, double droptol, double fill, double permtol, int32_t flags,
                           void *stream, om_ilu **out);
 
+/* The host factorisation of om_ilu_factor / om_ilutp_factor alone, on HOST
+ * arrays, with no device involved (A in CSR: rowptr int64[N+1], col int32,
+ * val interleaved complex128 doubles; rows sorted by column).  flags bits 0
+ * (compensation), 3 (equilibration) and 4 (total fill budget) as for
+ * om_ilu_factor; permtol > 0 pivots as om_ilutp_factor (not with bits 0 or
+ * 4).  The handle holds the strict L and strict U parts in CSR (position
+ * space), the diagonal of U, the column at each position (the identity
+ * without pivoting) and the scalings r, c (ones without equilibration):
+ * om_host_ilu_sizes gives the entry counts, om_host_ilu_export copies them
+ * to caller-owned HOST arrays of sizes N+1, nnz_l, 2 nnz_l, N+1,
+ * nnz_u_strict, 2 nnz_u_strict, 2N, N, N, N (any may be NULL).  Errors:
+ * OM_EINVAL, OM_ENOMEM. */
+typedef struct om_host_ilu om_host_ilu;
+om_status om_ilu_factor_host(int64_t N, const int64_t *rowptr, const int32_t *col, const double *val,
+                             double droptol, double fill, double permtol, int32_t flags, om_host_ilu **out);
+om_status om_host_ilu_sizes(const om_host_ilu *F, int64_t *nnz_l, int64_t *nnz_u_strict, int64_t *n_guarded,
+                            int64_t *n_swaps);
+om_status om_host_ilu_export(const om_host_ilu *F, int64_t *lp, int32_t *li, double *lx, int64_t *up,
+                             int32_t *ui, double *ux, double *diag, int32_t *q, double *r, double *c);
+void om_host_ilu_free(om_host_ilu *F);
+
 /* Pivoting of a factor: *pivoted = 1 for an om_ilutp_factor handle, the
  * number of column swaps, and the column at each position (HOST int32[N],
  * the identity without pivoting; synchronises the stream).  Any out pointer

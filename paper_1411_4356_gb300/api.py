@@ -197,6 +197,37 @@ def ilu_factor(A: Matrix, droptol: float, fill: float, compensate: bool = False,
     return ILU(out.value, A.nnz, A.N)
 
 
+def ilu_factor_host(rowptr, col, val, droptol: float, fill: float, permtol: float = 0.0, compensate: bool = False,
+                    equilibrate: bool = False, cap: str = "row") -> dict:
+    """The host factorisation of ilu_factor alone, on numpy CSR arrays, no
+    device involved (om_ilu_factor_host): a dict of numpy arrays (lp, li, lx,
+    up, ui, ux -- strict parts in position space --, diag, q, r, c) and the
+    counts n_guarded, n_swaps."""
+    lib = _lib.load()
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col, dtype=np.int32)
+    va = np.ascontiguousarray(val, dtype=np.complex128)
+    N = len(rp) - 1
+    flags = (1 if compensate else 0) | (8 if equilibrate else 0) | (16 if cap == "total" else 0)
+    h = ctypes.c_void_p()
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    check(lib.om_ilu_factor_host(N, vp(rp), vp(ci), vp(va), float(droptol), float(fill), float(permtol), flags,
+                                 ctypes.byref(h)), "om_ilu_factor_host")
+    try:
+        cnt = [ctypes.c_int64() for _ in range(4)]
+        check(lib.om_host_ilu_sizes(h, *[ctypes.byref(x) for x in cnt]), "om_host_ilu_sizes")
+        nl, nu, ng, ns = (x.value for x in cnt)
+        out = dict(lp=np.empty(N + 1, np.int64), li=np.empty(nl, np.int32), lx=np.empty(nl, np.complex128),
+                   up=np.empty(N + 1, np.int64), ui=np.empty(nu, np.int32), ux=np.empty(nu, np.complex128),
+                   diag=np.empty(N, np.complex128), q=np.empty(N, np.int32), r=np.empty(N), c=np.empty(N))
+        check(lib.om_host_ilu_export(h, *[vp(out[k]) for k in ("lp", "li", "lx", "up", "ui", "ux", "diag", "q",
+                                                                "r", "c")]), "om_host_ilu_export")
+    finally:
+        lib.om_host_ilu_free(h)
+    out["n_guarded"], out["n_swaps"] = ng, ns
+    return out
+
+
 def ilu_pivots(M: ILU, stream=None):
     """(pivoted, number of column swaps, q as a numpy int32 array: the column at each position)."""
     piv = ctypes.c_int32()

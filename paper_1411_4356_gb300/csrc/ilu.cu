@@ -942,3 +942,85 @@ extern "C" om_status om_ilu_info(const om_ilu *M, int64_t *nnz_l, int64_t *nnz_u
         if (levels_u) *levels_u = M->levels_u;
     });
 }
+
+// ---- the host factorisation alone, on host arrays (no device involved)
+
+struct om_host_ilu {
+    int64_t N = 0;
+    omss::HostTri L, U;  // strict parts, position space
+    std::vector<std::complex<double>> diag;
+    std::vector<int32_t> q;           // column at each position (identity without pivoting)
+    std::vector<double> r, c;         // equilibration scalings (ones without)
+    int64_t guarded = 0, swaps = 0;
+};
+
+extern "C" om_status om_ilu_factor_host(int64_t N, const int64_t *rowptr, const int32_t *col, const double *val,
+                                        double droptol, double fill, double permtol, int32_t flags,
+                                        om_host_ilu **out) {
+    return guarded([&] {
+        OM_REQUIRE(out && N >= 0 && (N == 0 || (rowptr && col && val)), "om_ilu_factor_host: bad argument");
+        OM_REQUIRE(droptol >= 0 && fill > 0 && permtol >= 0 && permtol <= 1, "om_ilu_factor_host: bad parameter");
+        OM_REQUIRE((flags & ~(1 | 8 | 16)) == 0, "om_ilu_factor_host: flags 1, 8 and 16 only");
+        OM_REQUIRE(!((flags & 16) && ((flags & 1) || permtol > 0)) && !((flags & 1) && permtol > 0),
+                   "om_ilu_factor_host: incompatible options");
+        *out = nullptr;
+        const int64_t nnz = N ? rowptr[N] : 0;
+        std::vector<int64_t> rp(rowptr, rowptr + N + 1);
+        std::vector<int32_t> ci(col, col + nnz);
+        std::vector<double2> va(nnz);
+        for (int64_t e = 0; e < nnz; ++e) va[e] = make_double2(val[2 * e], val[2 * e + 1]);
+        auto F = std::make_unique<om_host_ilu>();
+        F->N = N;
+        if (flags & 8) {
+            omss::equilibrate_host(N, rp, ci, va, F->r, F->c);
+        } else {
+            F->r.assign(N, 1.0);
+            F->c.assign(N, 1.0);
+        }
+        if (permtol > 0)
+            omss::ilutp_host(N, rp, ci, va, droptol, fill, permtol, F->L, F->U, F->diag, F->q, F->guarded, F->swaps);
+        else if (flags & 16)
+            omss::ilut_total_host(N, rp, ci, va, droptol, fill, F->L, F->U, F->diag, F->guarded);
+        else
+            omss::ilut_host(N, rp, ci, va, droptol, fill, (flags & 1) != 0, F->L, F->U, F->diag, F->guarded);
+        if (F->q.empty()) {
+            F->q.resize(N);
+            for (int64_t k = 0; k < N; ++k) F->q[k] = (int32_t)k;
+        }
+        *out = F.release();
+    });
+}
+
+extern "C" om_status om_host_ilu_sizes(const om_host_ilu *F, int64_t *nnz_l, int64_t *nnz_u_strict,
+                                       int64_t *n_guarded, int64_t *n_swaps) {
+    return guarded([&] {
+        OM_REQUIRE(F, "om_host_ilu_sizes: NULL handle");
+        if (nnz_l) *nnz_l = (int64_t)F->L.ci.size();
+        if (nnz_u_strict) *nnz_u_strict = (int64_t)F->U.ci.size();
+        if (n_guarded) *n_guarded = F->guarded;
+        if (n_swaps) *n_swaps = F->swaps;
+    });
+}
+
+extern "C" om_status om_host_ilu_export(const om_host_ilu *F, int64_t *lp, int32_t *li, double *lx, int64_t *up,
+                                        int32_t *ui, double *ux, double *diag, int32_t *q, double *r, double *c) {
+    return guarded([&] {
+        OM_REQUIRE(F, "om_host_ilu_export: NULL handle");
+        const int64_t N = F->N;
+        if (lp) std::copy(F->L.rp.begin(), F->L.rp.end(), lp);
+        if (li) std::copy(F->L.ci.begin(), F->L.ci.end(), li);
+        if (lx) std::copy(reinterpret_cast<const double *>(F->L.va.data()),
+                          reinterpret_cast<const double *>(F->L.va.data()) + 2 * F->L.va.size(), lx);
+        if (up) std::copy(F->U.rp.begin(), F->U.rp.end(), up);
+        if (ui) std::copy(F->U.ci.begin(), F->U.ci.end(), ui);
+        if (ux) std::copy(reinterpret_cast<const double *>(F->U.va.data()),
+                          reinterpret_cast<const double *>(F->U.va.data()) + 2 * F->U.va.size(), ux);
+        if (diag) std::copy(reinterpret_cast<const double *>(F->diag.data()),
+                            reinterpret_cast<const double *>(F->diag.data()) + 2 * N, diag);
+        if (q) std::copy(F->q.begin(), F->q.end(), q);
+        if (r) std::copy(F->r.begin(), F->r.end(), r);
+        if (c) std::copy(F->c.begin(), F->c.end(), c);
+    });
+}
+
+extern "C" void om_host_ilu_free(om_host_ilu *F) { delete F; }
