@@ -168,6 +168,12 @@ om_status om_permute(const om_matrix *A, void *stream, int32_t *perm_dev, om_mat
  * OM_ECUDA. */
 om_status om_permute_ex(const om_matrix *A, int32_t flags, void *stream, int32_t *perm_dev, om_matrix **A_rcm);
 
+/* The serial order of om_permute_ex (bit 0 clear) alone, on HOST CSR arrays
+ * (rowptr int64[N+1], col int32, rows sorted by column), with no device
+ * involved: perm (HOST int32[N]) = perm[new] = old.  Errors: OM_EINVAL,
+ * OM_ENOMEM. */
+om_status om_rcm_order_host(int64_t N, const int64_t *rowptr, const int32_t *col, int32_t *perm);
+
 /* ---- Sec. II: ILUT(d, p) ----------------------------------------------------
  * Row-wise incomplete LU of A (unit L, no pivoting).  In row i every entry
  * of modulus below droptol * ||row i of A||_inf is dropped (the diagonal is

@@ -197,6 +197,17 @@ def ilu_factor(A: Matrix, droptol: float, fill: float, compensate: bool = False,
     return ILU(out.value, A.nnz, A.N)
 
 
+def rcm_order_host(rowptr, col):
+    """The serial RCM order of the pattern of A + A^T on numpy CSR arrays, no
+    device involved (om_rcm_order_host): perm[new] = old."""
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col, dtype=np.int32)
+    perm = np.empty(len(rp) - 1, dtype=np.int32)
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    check(_lib.load().om_rcm_order_host(len(rp) - 1, vp(rp), vp(ci), vp(perm)), "om_rcm_order_host")
+    return perm
+
+
 def ilu_factor_host(rowptr, col, val, droptol: float, fill: float, permtol: float = 0.0, compensate: bool = False,
                     equilibrate: bool = False, cap: str = "row") -> dict:
     """The host factorisation of ilu_factor alone, on numpy CSR arrays, no

@@ -272,3 +272,14 @@ extern "C" om_status om_permute_ex(const om_matrix *A, int32_t flags, void *stre
 extern "C" om_status om_permute(const om_matrix *A, void *stream, int32_t *perm_dev, om_matrix **A_rcm) {
     return om_permute_ex(A, 1, stream, perm_dev, A_rcm);
 }
+
+// the serial order alone, on host arrays (no device involved)
+extern "C" om_status om_rcm_order_host(int64_t N, const int64_t *rowptr, const int32_t *col, int32_t *perm) {
+    return guarded([&] {
+        OM_REQUIRE(N >= 0 && perm && (N == 0 || (rowptr && col)), "om_rcm_order_host: bad argument");
+        std::vector<int64_t> rp(rowptr, rowptr + N + 1);
+        std::vector<int32_t> ci(col, col + (N ? rowptr[N] : 0));
+        std::vector<int32_t> order = rcm_order(N, rp, ci);
+        std::copy(order.begin(), order.end(), perm);
+    });
+}

@@ -91,3 +91,14 @@ def test_bad_options_are_rejected():
         api.ilu_factor_host(A.indptr, A.indices, A.data, 1e-4, 10.0, permtol=0.1, cap="total")
     with pytest.raises(OMError):
         api.ilu_factor_host(A.indptr, A.indices, A.data, 1e-4, 10.0, permtol=1.5)
+
+
+@pytest.mark.parametrize("Nc,Nm,prm,floor", [(1, 1, BASE, 1e-15), (2, 3, BASE, 1e-15), (4, 8, BASE, 1e-15),
+                                             (10, 20, BASE, 1e-15), (4, 60, FIG4, 0.0), (12, 30, BASE, 1e-15)])
+@pytest.mark.parametrize("mode", ["replace", "add"])
+def test_host_rcm_order(Nc, Nm, prm, floor, mode):
+    """The library's serial RCM walk against the oracle's, bit-exact, up to 129,600 rows."""
+    Lt, *_ = augmented(Params(Nc, Nm, *prm), mode, floor)
+    Lt = sp.csr_matrix(Lt)
+    Lt.sort_indices()
+    np.testing.assert_array_equal(api.rcm_order_host(Lt.indptr, Lt.indices), rcm_permutation(Lt))
