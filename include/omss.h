@@ -139,6 +139,14 @@ typedef struct om_ilu om_ilu;       /* ILU factors + sweep schedule on the devic
 om_status om_build_liouvillian(const om_params *params, const om_build_opts *opts,
                                void *stream, om_matrix **out);
 
+/* Row k of L (Eq. 3 in the basis of Eq. 4, without the trace row), from the
+ * closed form the assembly kernels evaluate, computed on the host with no
+ * device involved: its count (<= 21) columns (HOST int64) in increasing
+ * order and values (HOST interleaved complex128 doubles); exact zeros are
+ * left out.  opts->nth_floor as for om_build_liouvillian.  Errors: OM_EINVAL. */
+om_status om_liouvillian_row_host(const om_params *params, const om_build_opts *opts, int64_t k, int64_t *cols,
+                                  double *vals, int32_t *count);
+
 /* Host-side description of a matrix handle; any out pointer may be NULL. */
 om_status om_matrix_info(const om_matrix *A, int64_t *nrows, int64_t *nnz, double *w,
                          double *norm_inf);

@@ -50,6 +50,8 @@ SIGNATURES = {
     "om_ilu_factor": (c_i32, [c_vp, c_dbl, c_dbl, c_i32, c_vp, ctypes.POINTER(c_vp)]),
     "om_steady_state_sweep_nojump": (c_i32, [c_i32, c_vp, ctypes.POINTER(om_build_opts), c_i32,
                                              ctypes.POINTER(om_solve_opts), c_vp, c_vp, c_vp, c_i32, c_vp]),
+    "om_liouvillian_row_host": (c_i32, [ctypes.POINTER(om_params), ctypes.POINTER(om_build_opts), c_i64, c_vp, c_vp,
+                                        ctypes.POINTER(c_i32)]),
     "om_rcm_order_host": (c_i32, [c_i64, c_vp, c_vp, c_vp]),
     "om_ilu_factor_host": (c_i32, [c_i64, c_vp, c_vp, c_vp, c_dbl, c_dbl, c_dbl, c_i32, ctypes.POINTER(c_vp)]),
     "om_host_ilu_sizes": (c_i32, [c_vp] + [ctypes.POINTER(c_i64)] * 4),

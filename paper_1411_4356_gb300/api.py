@@ -197,6 +197,21 @@ def ilu_factor(A: Matrix, droptol: float, fill: float, compensate: bool = False,
     return ILU(out.value, A.nnz, A.N)
 
 
+def liouvillian_row_host(params: SystemParams, k: int, nth_floor: float = 1e-15):
+    """Row k of L from the assembly's closed form, on the host (om_liouvillian_row_host):
+    (columns int64, values complex128) as numpy arrays."""
+    cols = np.empty(32, dtype=np.int64)
+    vals = np.empty(32, dtype=np.complex128)
+    cnt = ctypes.c_int32()
+    p = to_om_params(params)
+    o = om_build_opts(0, nth_floor)
+    check(_lib.load().om_liouvillian_row_host(ctypes.byref(p), ctypes.byref(o), int(k),
+                                              cols.ctypes.data_as(ctypes.c_void_p),
+                                              vals.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cnt)),
+          "om_liouvillian_row_host")
+    return cols[:cnt.value].copy(), vals[:cnt.value].copy()
+
+
 def rcm_order_host(rowptr, col):
     """The serial RCM order of the pattern of A + A^T on numpy CSR arrays, no
     device involved (om_rcm_order_host): perm[new] = old."""

@@ -577,3 +577,38 @@ extern "C" om_status om_liouvillian_apply(const om_matrix *A, const double *x, d
                                as_stream(stream));
     });
 }
+
+// one row of L (Eq. 3 in the basis of Eq. 4, no trace row) from the same
+// closed form the assembly kernels use, evaluated on the host
+extern "C" om_status om_liouvillian_row_host(const om_params *params, const om_build_opts *opts, int64_t k,
+                                             int64_t *cols, double *vals, int32_t *count) {
+    return guarded([&] {
+        OM_REQUIRE(params && opts && cols && vals && count, "om_liouvillian_row_host: NULL argument");
+        const om_params &p = *params;
+        OM_REQUIRE(p.Nc >= 1 && p.Nm >= 1 && p.Q_m > 0.0, "om_liouvillian_row_host: bad parameters");
+        const int64_t n = (int64_t)p.Nc * p.Nm;
+        OM_REQUIRE(k >= 0 && k < n * n, "om_liouvillian_row_host: row out of range");
+        Model M;
+        M.Nc = p.Nc;
+        M.Nm = p.Nm;
+        M.n = (int32_t)n;
+        M.omega_m = p.omega_m;
+        M.Delta = p.Delta;
+        M.kappa = p.kappa;
+        M.g0 = p.g0;
+        M.E = p.E;
+        const double nth = (p.n_th == 0.0 && opts->nth_floor > 0.0) ? opts->nth_floor : p.n_th;
+        const double Gm = p.omega_m / p.Q_m;
+        M.gam_down = Gm * (1.0 + nth);
+        M.gam_up = Gm * nth;
+        std::vector<double> vt_host;
+        M.vband = variant_bands(p, vt_host);
+        M.vt = M.vband ? vt_host.data() : nullptr;
+        double2 v[kMaxRow];
+        *count = liouvillian_row(M, k, cols, v);
+        for (int t = 0; t < *count; ++t) {
+            vals[2 * t] = v[t].x;
+            vals[2 * t + 1] = v[t].y;
+        }
+    });
+}
